@@ -1,0 +1,153 @@
+"""FP64 CPU oracle of the direct kinematic scattering sum.
+
+TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The GPU library
+never imports it, and this package imports nothing from the library.
+
+The arithmetic lives in ``scatter_oracle.c`` (plain loops in double precision,
+OpenMP over reflections); this module compiles it with gcc into
+``oracle/lib/liboracle.so`` and wraps it with ctypes and numpy.
+
+Every function below follows the paper's definitions:
+  amplitude    Eq. 2 with occupancies (Section 3) and per-species factors
+               (Section 4.2)
+  fresnel      substrate reflection/transmission (Section 3, pynx.gid)
+  dwba         four-beam grazing-incidence sum (Section 4.3; the formula is a
+               reading, the paper prints none)
+  loss_grad    L = sum (|A|^2 - I_obs)^2 and its analytic gradient
+  fd_grad      central finite differences of L (a second route to the gradient)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import pathlib
+import subprocess
+
+import numpy as np
+
+HERE = pathlib.Path(__file__).resolve().parent
+SRC = HERE / "scatter_oracle.c"
+LIBDIR = HERE / "lib"
+LIB = LIBDIR / "liboracle.so"
+
+NCOEF = 12  # a0..a3, b0..b3, c, f', f'', B_dw
+
+_lib = None
+
+
+def build(force: bool = False) -> pathlib.Path:
+    """Compile the oracle with gcc -O2 -fopenmp (no -ffast-math)."""
+    if force or not LIB.exists() or LIB.stat().st_mtime < SRC.stat().st_mtime:
+        LIBDIR.mkdir(parents=True, exist_ok=True)
+        tmp = LIBDIR / f"liboracle.{os.getpid()}.so"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(tmp), str(SRC), "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle build failed:\n{r.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(str(build()))
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.oracle_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P]
+        lib.oracle_form_factor.argtypes = [P, f64, P, P]
+        lib.oracle_fresnel.argtypes = [f64, f64, f64, P, P]
+        lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
+        lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
+        lib.oracle_fd_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, i64, P, f64, P]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _f64(a, shape_last=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape_last is not None:
+        a = a.reshape(-1, shape_last)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _atoms(xyz, species, occ, coef):
+    xyz = _f64(xyz, 3)
+    n = xyz.shape[0]
+    sp = None if species is None else np.ascontiguousarray(np.asarray(species, dtype=np.int32).reshape(n))
+    w = None if occ is None else _f64(occ).reshape(n)
+    coef = _f64(coef, NCOEF)
+    if sp is not None and n and (sp.min() < 0 or sp.max() >= coef.shape[0]):
+        raise ValueError("species index out of range")
+    return xyz, sp, w, coef
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def form_factor(coef, q_inv_angstrom: float) -> complex:
+    """f(|S|) of one species; q = |S| in 1/Angstrom."""
+    c = _f64(coef).reshape(NCOEF)
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_form_factor(_ptr(c), float(q_inv_angstrom), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+def amplitude(xyz, S, coef, lattice_a, species=None, occ=None) -> np.ndarray:
+    """A(S) of Eq. 2 for S [M,3] (r.l.u.), positions [N,3] (lattice units)."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    S = _f64(S, 3)
+    out = np.zeros((S.shape[0], 2))
+    _load().oracle_amplitude(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                             float(lattice_a), S.shape[0], _ptr(S), _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def fresnel(alpha: float, delta: float, beta: float) -> tuple[complex, complex]:
+    R = np.zeros(2)
+    T = np.zeros(2)
+    _load().oracle_fresnel(float(alpha), float(delta), float(beta), _ptr(R), _ptr(T))
+    return complex(R[0], R[1]), complex(T[0], T[1])
+
+
+def dwba(xyz, pts, coef, lattice_a, wavelength, alpha_i, delta, beta, species=None, occ=None) -> np.ndarray:
+    """Four-term DWBA amplitude at points (h, k, alpha_f) [M,3]."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    pts = _f64(pts, 3)
+    out = np.zeros((pts.shape[0], 2))
+    _load().oracle_dwba(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                        float(lattice_a), float(wavelength), float(alpha_i), float(delta), float(beta),
+                        pts.shape[0], _ptr(pts), _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def loss_grad(xyz, S, I_obs, coef, lattice_a, species=None, occ=None, grad=True):
+    """(L, dL/dr [N,3] or None) for L = sum (|A|^2 - I_obs)^2."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    S = _f64(S, 3)
+    I_obs = _f64(I_obs).reshape(S.shape[0])
+    loss = ctypes.c_double()
+    g = np.zeros((xyz.shape[0], 3)) if grad else None
+    _load().oracle_loss_grad(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                             float(lattice_a), S.shape[0], _ptr(S), _ptr(I_obs), ctypes.byref(loss), _ptr(g))
+    return loss.value, g
+
+
+def fd_grad(xyz, S, I_obs, coef, lattice_a, atoms, h=1e-5, species=None, occ=None) -> np.ndarray:
+    """Central-difference gradient of L for the selected atoms, [len(atoms),3]."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    S = _f64(S, 3)
+    I_obs = _f64(I_obs).reshape(S.shape[0])
+    sel = np.ascontiguousarray(np.asarray(atoms, dtype=np.int64))
+    out = np.zeros((sel.shape[0], 3))
+    _load().oracle_fd_grad(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                           float(lattice_a), S.shape[0], _ptr(S), _ptr(I_obs), sel.shape[0], _ptr(sel),
+                           float(h), _ptr(out))
+    return out

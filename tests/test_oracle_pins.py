@@ -1,0 +1,351 @@
+"""Pins of the FP64 oracle to results fixed by the paper and by mathematics.
+
+None of these tests re-evaluates the oracle's own code path: each compares
+it with a closed form (geometric series of a parallelepiped, Section 2.3),
+an invariant of Eq. 2 (Friedel, translation, species factoring, occupancy,
+permutation), a high-precision brute force on tiny inputs, textbook Fresnel
+coefficients or wave-vector kinematics (Section 4.3), or an independent
+route to the gradient.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1010_2641_gb300 import workloads as W
+
+A_LAT = W.LATTICE_A
+
+
+def dirichlet(N, S):
+    """Closed form of the geometric series sum_{n=0}^{N-1} exp(2 i pi S n).
+
+    n is an integer, so only sigma = S - rint(S) matters:
+    exp(i pi (N-1) sigma) sin(pi N sigma) / sin(pi sigma), with the series
+    N (1 - pi^2 (N^2-1) sigma^2 / 6) for |sigma| < 1e-9."""
+    S = np.asarray(S, dtype=np.float64)
+    sig = S - np.rint(S)
+    small = np.abs(sig) < 1e-9
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ratio = np.where(small, N * (1.0 - (math.pi ** 2) * (N * N - 1) * sig * sig / 6.0),
+                         np.sin(math.pi * N * sig) / np.sin(math.pi * sig))
+    return np.exp(1j * math.pi * (N - 1) * sig) * ratio
+
+
+def parallelepiped_closed_form(n, S):
+    S = np.asarray(S)
+    return dirichlet(n[0], S[:, 0]) * dirichlet(n[1], S[:, 1]) * dirichlet(n[2], S[:, 2])
+
+
+def unit_coef():
+    return W.unit_species()[None, :]
+
+
+# ----------------------------------------------------------------------------
+# Eq. 2 against closed forms
+# ----------------------------------------------------------------------------
+
+def test_dirichlet_cube_tiny_config():
+    """10x10x10 simple cubic, f=1, 32^3 grid spanning +-0.5 around (0,0,4)."""
+    xyz = W.simple_cubic((10, 10, 10))
+    ax = [W.linspace_axis(c, 32, half_width=0.5) for c in (0.0, 0.0, 4.0)]
+    S = W.grid_points(ax)
+    A = oracle.amplitude(xyz, S, unit_coef(), A_LAT)
+    ref = parallelepiped_closed_form((10, 10, 10), S)
+    assert np.max(np.abs(A - ref)) < 1e-9 * 1000
+    assert np.linalg.norm(A - ref) / np.linalg.norm(ref) < 1e-12
+
+
+@pytest.mark.parametrize("n", [(3, 5, 7), (1, 4, 9)])
+def test_dirichlet_box_random_S(n):
+    rng = np.random.default_rng(7)
+    xyz = W.simple_cubic(n)
+    S = rng.uniform(-3.0, 3.0, (500, 3))
+    S[:20] = np.rint(S[:20])  # exact reciprocal-lattice nodes: |A| = N
+    A = oracle.amplitude(xyz, S, unit_coef(), A_LAT)
+    ref = parallelepiped_closed_form(n, S)
+    assert np.max(np.abs(A - ref)) < 1e-11 * np.prod(n)
+    assert np.allclose(np.abs(A[:20]), np.prod(n), rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1000, 10000, 100000])
+@pytest.mark.parametrize("offset", [0.0, 0.00037])
+def test_linear_chain_accuracy_test(N, offset):
+    """Section 2.3: chain at 0..N-1, H every 0.001 r.l.u. around H=1, versus
+    sin(pi N H)/sin(pi H) in full complex form (the paper's grid puts every
+    point but the peak on a zero of the kernel; the offset grid does not)."""
+    xyz = W.linear_chain(N)
+    H = 0.95 + offset + 0.001 * np.arange(100)
+    S = np.stack([H, np.zeros_like(H), np.zeros_like(H)], 1)
+    A = oracle.amplitude(xyz, S, unit_coef(), A_LAT)
+    ref = dirichlet(N, H)
+    # phases reach 1e5 cycles: FP64 keeps ~1e-11 rad per term
+    assert np.max(np.abs(A - ref)) < 1e-9 * N
+    peak = np.argmin(np.abs(H - 1.0))
+    if offset == 0.0:
+        assert abs(abs(A[peak]) - N) < 1e-9 * N
+
+
+# ----------------------------------------------------------------------------
+# High-precision brute force on tiny inputs
+# ----------------------------------------------------------------------------
+
+def test_brute_force_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    rng = np.random.default_rng(11)
+    n_atoms, n_s = 9, 15
+    xyz = rng.uniform(-6, 6, (n_atoms, 3))
+    species = rng.integers(0, 2, n_atoms).astype(np.int32)
+    occ = rng.uniform(0.2, 1.5, n_atoms)
+    coef = np.stack([W.species_coefficients(14, 0.3, 0.7, 0.4), W.species_coefficients(32, -1.2, 2.5, 0.9)])
+    coef[1, 4:8] = [0.2, 1.7, 9.0, 30.0]
+    S = rng.uniform(-5, 5, (n_s, 3))
+    A = oracle.amplitude(xyz, S, coef, A_LAT, species=species, occ=occ)
+    for m in range(n_s):
+        Sm = [mp.mpf(float(v)) for v in S[m]]
+        # Bragg's law: d = a / |hkl|, sin(theta)/lambda = 1 / (2 d)
+        d = mp.mpf(A_LAT) / mp.sqrt(sum(v * v for v in Sm))
+        s2 = (1 / (2 * d)) ** 2
+        tot = mp.mpc(0)
+        for j in range(n_atoms):
+            c = coef[species[j]]
+            f0 = sum(mp.mpf(float(c[i])) * mp.e ** (-mp.mpf(float(c[4 + i])) * s2) for i in range(4)) + mp.mpf(float(c[8]))
+            f = (f0 + mp.mpf(float(c[9])) + 1j * mp.mpf(float(c[10]))) * mp.e ** (-mp.mpf(float(c[11])) * s2)
+            x = sum(Sm[i] * mp.mpf(float(xyz[j, i])) for i in range(3))
+            tot += mp.mpf(float(occ[j])) * f * mp.expjpi(2 * x)
+        ref = complex(tot)
+        assert abs(A[m] - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+# ----------------------------------------------------------------------------
+# Invariants of Eq. 2
+# ----------------------------------------------------------------------------
+
+def _random_problem(seed, n_atoms=200, n_s=300, real_f=False):
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(-8, 8, (n_atoms, 3))
+    species = rng.integers(0, 2, n_atoms).astype(np.int32)
+    occ = rng.uniform(0.5, 1.0, n_atoms)
+    coef = W.si_ge_species()
+    if real_f:
+        coef[:, 10] = 0.0
+    S = rng.uniform(-4, 4, (n_s, 3))
+    return xyz, species, occ, coef, S
+
+
+def test_friedel_symmetry():
+    xyz, sp, occ, coef, S = _random_problem(1, real_f=True)
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, occ)
+    Am = oracle.amplitude(xyz, -S, coef, A_LAT, sp, occ)
+    assert np.max(np.abs(Am - np.conj(A))) < 1e-11 * np.max(np.abs(A))
+
+
+def test_friedel_broken_by_anomalous_term():
+    """With f'' != 0 Friedel's law must fail: a check that the imaginary
+    part of f enters at all."""
+    xyz, sp, occ, coef, S = _random_problem(1, real_f=False)
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, occ)
+    Am = oracle.amplitude(xyz, -S, coef, A_LAT, sp, occ)
+    assert np.max(np.abs(Am - np.conj(A))) > 1e-3 * np.max(np.abs(A))
+
+
+def test_translation_phase():
+    xyz, sp, occ, coef, S = _random_problem(2)
+    t = np.array([0.3, -1.7, 2.25])
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, occ)
+    At = oracle.amplitude(xyz + t, S, coef, A_LAT, sp, occ)
+    assert np.max(np.abs(At - np.exp(2j * math.pi * (S @ t)) * A)) < 1e-11 * np.max(np.abs(A))
+
+
+def test_species_factoring():
+    """A = sum_s f_s(|S|) * sum_{j in s} w_j exp(2 i pi S.r_j)  (Section 4.2).
+    f_s(|S|) is obtained as the amplitude of one atom of species s at the
+    origin, and the per-species sums with f = 1."""
+    xyz, sp, occ, coef, S = _random_problem(3)
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, occ)
+    tot = np.zeros_like(A)
+    for s in range(coef.shape[0]):
+        f_s = oracle.amplitude(np.zeros((1, 3)), S, coef[s:s + 1], A_LAT)
+        m = sp == s
+        tot += f_s * oracle.amplitude(xyz[m], S, unit_coef(), A_LAT, occ=occ[m])
+    assert np.max(np.abs(A - tot)) < 1e-11 * np.max(np.abs(A))
+
+
+def test_form_factor_values():
+    c = W.species_coefficients(32.0, -1.6, 0.9, 0.6)
+    f0 = oracle.form_factor(c, 0.0)
+    assert abs(f0 - complex(32.0 - 1.6, 0.9)) < 1e-13
+    # single Gaussian, exp(-b s^2) at the (004) reflection: Bragg's law
+    # d = a/4, sin(theta)/lambda = 1/(2d)
+    g = np.zeros(12)
+    g[0], g[4] = 1.0, 2.5
+    S = np.array([[0.0, 0.0, 4.0]])
+    s = 1.0 / (2.0 * A_LAT / 4.0)
+    A = oracle.amplitude(np.zeros((1, 3)), S, g[None], A_LAT)
+    assert abs(A[0] - math.exp(-2.5 * s * s)) < 1e-14
+    # Debye-Waller alone
+    g = np.zeros(12)
+    g[8], g[11] = 1.0, 0.7
+    A = oracle.amplitude(np.zeros((1, 3)), S, g[None], A_LAT)
+    assert abs(A[0] - math.exp(-0.7 * s * s)) < 1e-14
+
+
+def test_occupancy():
+    xyz, sp, occ, coef, S = _random_problem(4, n_atoms=50)
+    w = occ.copy()
+    w[7] = 2.0
+    w[9] = 0.0
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, w)
+    keep = np.ones(len(xyz), bool)
+    keep[9] = False
+    xyz2 = np.concatenate([xyz[keep], xyz[7:8]])
+    sp2 = np.concatenate([sp[keep], sp[7:8]])
+    w2 = np.concatenate([w[keep], [1.0]])
+    w2[list(np.nonzero(keep)[0]).index(7)] = 1.0
+    A2 = oracle.amplitude(xyz2, S, coef, A_LAT, sp2, w2)
+    assert np.max(np.abs(A - A2)) < 1e-11 * np.max(np.abs(A))
+
+
+def test_permutation_invariance():
+    xyz, sp, occ, coef, S = _random_problem(5)
+    p = np.random.default_rng(0).permutation(len(xyz))
+    A = oracle.amplitude(xyz, S, coef, A_LAT, sp, occ)
+    Ap = oracle.amplitude(xyz[p], S, coef, A_LAT, sp[p], occ[p])
+    assert np.max(np.abs(A - Ap)) < 1e-11 * np.max(np.abs(A))
+
+
+# ----------------------------------------------------------------------------
+# Fresnel coefficients and the four-beam DWBA sum (Section 4.3)
+# ----------------------------------------------------------------------------
+
+def fresnel_textbook(alpha, delta, beta):
+    """s-polarised Fresnel reflection with angles from the surface normal:
+    r = (cos ti - n cos tt) / (cos ti + n cos tt), Snell sin ti = n sin tt."""
+    n = 1.0 - delta + 1j * beta
+    ti = math.pi / 2 - alpha
+    cos_tt = np.sqrt(1.0 - (math.sin(ti) / n) ** 2 + 0j)
+    if (n * cos_tt).imag < 0:  # wave decaying into the substrate
+        cos_tt = -cos_tt
+    r = (math.cos(ti) - n * cos_tt) / (math.cos(ti) + n * cos_tt)
+    return r, 1.0 + r
+
+
+@pytest.mark.parametrize("alpha_deg", [0.01, 0.1, 0.2, 0.25, 0.3, 1.0, 5.0])
+def test_fresnel_textbook(alpha_deg):
+    a = math.radians(alpha_deg)
+    R, T = oracle.fresnel(a, 1e-5, 1e-7)
+    r_ref, t_ref = fresnel_textbook(a, 1e-5, 1e-7)
+    assert abs(R - r_ref) < 1e-9
+    assert abs(T - (1 + R)) < 1e-15
+    assert abs(T - t_ref) < 1e-9
+
+
+def test_fresnel_limits():
+    delta = 1e-5
+    a_c = math.acos(1.0 - delta)  # cos(alpha_c) = n for beta = 0
+    for a in (0.1 * a_c, 0.5 * a_c, 0.99 * a_c):
+        R, _ = oracle.fresnel(a, delta, 0.0)
+        assert abs(abs(R) - 1.0) < 1e-12  # total external reflection
+    for a in (1.01 * a_c, 2 * a_c):
+        R, _ = oracle.fresnel(a, delta, 0.0)
+        assert abs(R) < 1.0 - 1e-6 and abs(R.imag) < 1e-12
+    R, _ = oracle.fresnel(1e-9, delta, 1e-7)
+    assert abs(R + 1.0) < 1e-3  # grazing limit R -> -1
+    a = math.radians(5.0)
+    R, _ = oracle.fresnel(a, delta, 1e-7)
+    asym = (delta - 1e-7j) / (2 * math.sin(a) ** 2)
+    assert abs(R - asym) < 2e-2 * abs(asym)
+
+
+def _kin_S(h, k, alpha_i, alpha_f, lam, a, inc_reflected, exit_reflected):
+    """S (r.l.u.) of one DWBA beam from wave vectors (|k| = 1/lambda).
+    The substrate mirrors the z component of a wave."""
+    ki_z = -math.sin(alpha_i) / lam
+    kf_z = math.sin(alpha_f) / lam
+    if inc_reflected:
+        ki_z = -ki_z
+    if exit_reflected:
+        kf_z = -kf_z
+    return np.array([h, k, (kf_z - ki_z) * a])
+
+
+def test_dwba_reduces_to_kinematic_without_substrate():
+    rng = np.random.default_rng(21)
+    xyz = rng.uniform(-5, 5, (60, 3))
+    coef = W.si_ge_species()[:1]
+    lam, ai = W.WAVELENGTH_10KEV, W.GID_ALPHA_I
+    pts = np.stack([rng.uniform(3.8, 4.1, 40), rng.uniform(-0.1, 0.1, 40),
+                    np.radians(rng.uniform(0.05, 1.0, 40))], 1)
+    A = oracle.dwba(xyz, pts, coef, A_LAT, lam, ai, 0.0, 0.0)
+    S1 = np.array([_kin_S(p[0], p[1], ai, p[2], lam, A_LAT, False, False) for p in pts])
+    ref = oracle.amplitude(xyz, S1, coef, A_LAT)
+    assert np.max(np.abs(A - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_dwba_four_beams():
+    rng = np.random.default_rng(22)
+    xyz = rng.uniform(-5, 5, (60, 3))
+    xyz[:, 2] = np.abs(xyz[:, 2])
+    sp = rng.integers(0, 2, 60).astype(np.int32)
+    coef = W.si_ge_species()
+    lam, ai, d, b = W.WAVELENGTH_10KEV, W.GID_ALPHA_I, 3e-5, 2e-6
+    pts = np.stack([rng.uniform(3.8, 4.1, 30), rng.uniform(-0.1, 0.1, 30),
+                    np.radians(rng.uniform(0.02, 1.0, 30))], 1)
+    A = oracle.dwba(xyz, pts, coef, A_LAT, lam, ai, d, b, species=sp)
+    Ri, _ = fresnel_textbook(ai, d, b)
+    for m, p in enumerate(pts):
+        Rf, _ = fresnel_textbook(p[2], d, b)
+        beams = [(False, False, 1.0), (True, False, Ri), (False, True, Rf), (True, True, Ri * Rf)]
+        tot = 0j
+        for inc_r, exit_r, wgt in beams:
+            S = _kin_S(p[0], p[1], ai, p[2], lam, A_LAT, inc_r, exit_r)[None]
+            tot += wgt * oracle.amplitude(xyz, S, coef, A_LAT, species=sp)[0]
+        assert abs(A[m] - tot) < 1e-9 * max(1.0, abs(tot))
+
+
+# ----------------------------------------------------------------------------
+# Misfit gradient: two routes and closed forms
+# ----------------------------------------------------------------------------
+
+def test_gradient_two_atoms_closed_form():
+    """Two atoms, f = 1: |A|^2 = 2 + 2 cos(2 pi S.(r1 - r2)), so
+    dL/dr1 = sum_S 2 (|A|^2 - I) (-2 sin(2 pi S.(r1-r2))) 2 pi S."""
+    rng = np.random.default_rng(31)
+    xyz = np.array([[0.3, -0.2, 1.1], [1.4, 0.9, -0.6]])
+    S = rng.uniform(-2, 2, (64, 3))
+    I_obs = rng.uniform(0, 4, 64)
+    L, g = oracle.loss_grad(xyz, S, I_obs, unit_coef(), A_LAT)
+    ph = 2 * math.pi * (S @ (xyz[0] - xyz[1]))
+    I = 2 + 2 * np.cos(ph)
+    assert abs(L - np.sum((I - I_obs) ** 2)) < 1e-10 * L
+    g1 = (2 * (I - I_obs) * (-2 * np.sin(ph)) * 2 * math.pi) @ S
+    assert np.allclose(g[0], g1, rtol=1e-11, atol=1e-9)
+    assert np.allclose(g[1], -g1, rtol=1e-11, atol=1e-9)
+
+
+def test_gradient_vs_finite_differences():
+    rng = np.random.default_rng(32)
+    c = W.fcc_sphere(radius_cells=2.6, seed=5)
+    S = W.grid_points([W.linspace_axis(0.0, 6, step=0.05), W.linspace_axis(0.0, 6, step=0.05),
+                       W.linspace_axis(4.0, 8, step=0.05)])
+    pert = W.perturbed_copy(c, 0.03, seed=6)
+    I_obs = np.abs(oracle.amplitude(pert.xyz, S, c.coef, A_LAT, pert.species)) ** 2
+    occ = rng.uniform(0.5, 1.0, len(c.xyz))
+    L, g = oracle.loss_grad(c.xyz, S, I_obs, c.coef, A_LAT, c.species, occ)
+    sel = rng.choice(len(c.xyz), 12, replace=False)
+    for h in (1e-5, 5e-6):
+        fd = oracle.fd_grad(c.xyz, S, I_obs, c.coef, A_LAT, sel, h=h, species=c.species, occ=occ)
+        assert np.max(np.abs(fd - g[sel])) < 1e-6 * np.max(np.abs(g[sel]))
+
+
+def test_gradient_translation_invariance():
+    """L depends on |A|^2 only, which a global translation leaves unchanged,
+    so the gradients of all atoms sum to zero."""
+    c = W.fcc_sphere(radius_cells=2.6, seed=7)
+    rng = np.random.default_rng(33)
+    S = rng.uniform(-0.3, 0.3, (150, 3)) + np.array([0, 0, 4.0])
+    I_obs = rng.uniform(0, 1e4, 150)
+    L, g = oracle.loss_grad(c.xyz, S, I_obs, c.coef, A_LAT, c.species)
+    assert np.max(np.abs(g.sum(0))) < 1e-10 * np.sum(np.abs(g))
