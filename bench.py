@@ -1,0 +1,388 @@
+"""Benchmark of the direct scattering sum on one GB300 (or N under torchrun).
+
+Workload (one step = one pass of the hot path over the synthetic input):
+strained spherical fcc nanocrystal of 134,009 atoms (radius 20 cells,
+Si-like core / Ge-like shell, radial strain + thermal noise) scattering onto
+a 256 x 256 x 64 grid of S points (step 0.002 r.l.u.) around (004):
+per-call prep (centring, split phase) + the generic FP32/MUFU kernel +
+epilogue, 5.6e11 atom-reflection pairs per step.
+
+Metric: atom-reflection pairs per second (whole job, all ranks), the paper's
+"reflections x atoms / s" (Section 2.2).  Each rank runs its own full
+instance (weak scaling, no collective on the data path).
+
+JSON line keys beyond the base contract:
+  roofline      dominant kernel (generic) against the MUFU bound
+                16 sin/cos ops / SM / clk -> 8 pairs / SM / clk x SMs x clock
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample
+  accuracy      relative L2 error of the GPU map vs the oracle on that sample
+  e2e           the same metric through the public API with host buffers
+                (positions H2D from pinned memory, map D2H every step)
+  paths         other rows measured on their own workloads (FP64 kernel,
+                adjoint) when --paths is given
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import pathlib
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "atom·reflections/s at ≤1e-4 rel err vs FP64 oracle; fraction of FP32/MUFU peak"
+UNIT = "atom·reflections/s"
+MUFU_SINCOS_PER_SM_CLK = 16.0   # measured (scatter_microbench kind 0): 15.97
+MUFU_OPS_PER_PAIR = 2.0         # one sin + one cos per (atom, reflection)
+
+
+def workload():
+    from paper_1010_2641_gb300 import workloads as W
+    c = W.fcc_sphere()
+    axes = [W.linspace_axis(0.0, 256, step=0.002), W.linspace_axis(0.0, 256, step=0.002),
+            W.linspace_axis(4.0, 64, step=0.002)]
+    return c, axes
+
+
+WORKLOAD_NAME = ("strained fcc sphere r=20 cells (134009 atoms, 2 species) x 256x256x64 S grid "
+                 "around (004), step 0.002 r.l.u.")
+
+
+def sample_indices(n_s: int, n: int, seed: int = 7):
+    return np.sort(np.random.default_rng(seed).choice(n_s, n, replace=False))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = ROOT / "gpurun_out" / f"clocks_rank{gpu_index}.csv"
+
+    def start(self):
+        try:
+            self.path.parent.mkdir(exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        for line in self.path.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# profile summary -> traffic of the dominant kernel (null if stale)
+# ---------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("forward.cu", "device_common.cuh", "plan.h"):
+        h.update((ROOT / "paper_1010_2641_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic():
+    """dram bytes per launch of the generic kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = ROOT / "profiles" / "generic_strained_sphere.md"
+    if not p.exists():
+        return None
+    text = p.read_text()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(source sha1 ([0-9a-f]+)\)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(c, S_sample):
+    import oracle
+    from paper_1010_2641_gb300 import workloads as W
+    return oracle.amplitude(c.xyz, S_sample, c.coef, W.LATTICE_A, species=c.species)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1010_2641_gb300 import workloads as W
+    oracle.build()
+    c, axes = workload()
+    n_s = 256 * 256 * 64
+    n_sample = args.ref_sample
+    idx = sample_indices(n_s, n_sample, seed=1)
+    S = W.grid_points(axes)[idx]
+    for _ in range(args.warmup):
+        oracle_step(c, S)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(c, S)
+        times.append(time.perf_counter() - t0)
+    pairs = len(c.xyz) * n_sample
+    v = pairs / float(np.mean(times))
+    cores = oracle.num_threads()
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "n_atoms": len(c.xyz), "n_s": n_s,
+                                           "sample_points": n_sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n_sample} of {n_s} grid points (seeded), all {len(c.xyz)} atoms"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    from paper_1010_2641_gb300 import api
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c, axes = workload()
+    n_atoms, n_s = len(c.xyz), 256 * 256 * 64
+    pairs = n_atoms * n_s
+    cache = str(ROOT / "gpurun_out" / "tune_cache.jsonl") if args.autotune else None
+    plan = api.Plan(c.coef, 5.43, n_atoms, axes=axes, atom_species=c.species, timing=True,
+                    autotune=args.autotune, tune_cache=cache)
+    info = plan.info()
+    xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
+    A = torch.empty(n_s, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        plan.amplitude(xyz, out=A)
+    torch.cuda.synchronize()
+    plan.check()
+
+    # ---- device-timed region: K steps, L2 flushed between steps -------------
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms, launches = [], 0
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.amplitude(xyz, out=A)
+        ev[i][1].record(stream)
+        ms_k, n_k = plan.timing()
+        kern_ms.append(ms_k)
+        launches += n_k
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = float(np.mean(step_ms))
+    t_kern = float(np.mean(kern_ms))
+    if world > 1:
+        t = torch.tensor([t_step, t_kern], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step, t_kern = t.tolist()
+    value = world * pairs / (t_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers -------------------
+    xyz_host = torch.tensor(c.xyz, dtype=torch.float64).pin_memory()
+    A_host = torch.empty(n_s, dtype=torch.complex64).pin_memory()
+    xyz_dev = torch.empty_like(xyz)
+    for _ in range(2):
+        xyz_dev.copy_(xyz_host, non_blocking=True)
+        plan.amplitude(xyz_dev, out=A)
+        A_host.copy_(A, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for i in range(max(2, args.steps // 2)):
+        flush.zero_()
+        e0.record(stream)
+        xyz_dev.copy_(xyz_host, non_blocking=True)
+        plan.amplitude(xyz_dev, out=A)
+        A_host.copy_(A, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = t.item()
+
+    # ---- roofline of the dominant kernel ----------------------------------------
+    sm_mhz = clk["sm_mhz"] if clk else None
+    n_sm = info["n_sm"]
+    roof = None
+    if sm_mhz:
+        peak = n_sm * MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR * sm_mhz * 1e6 / 1e9  # Gpair/s
+        achieved = pairs / (t_kern * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(),
+                "kernel": "k_generic (MUFU sin/cos, 16 ops/SM/clk)",
+                "kernel_ms": t_kern, "peak_basis": f"{n_sm} SMs x 8 pairs/SM/clk x {sm_mhz:.0f} MHz (median sampled)"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "n_atoms": n_atoms, "n_s": n_s, "pairs_per_step": pairs,
+                      "path": "generic", "threads": info["threads"], "points_per_thread": info["points_per_thread"],
+                      "split_k": info["split_k"], "l2": "flushed between steps (256 MB write, outside the events)",
+                      "parallelism": f"weak x{world} (independent instance per GPU)"},
+           "roofline": roof, "clocks": clk, "gpu_launches": launches,
+           "e2e": {"value": world * pairs / (t_e2e * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(xyz_host.numel() * 8), "d2h_bytes_per_step": int(A_host.numel() * 8)}}
+
+    # ---- CPU baseline + accuracy on a bounded sample (rank 0, N=1) -------------
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        from paper_1010_2641_gb300 import workloads as W
+        oracle.build()
+        idx = sample_indices(n_s, args.cpu_sample)
+        S = W.grid_points(axes)[idx]
+        t0 = time.perf_counter()
+        ref = oracle_step(c, S)
+        dt = time.perf_counter() - t0
+        got = A.cpu().numpy()[idx].astype(np.complex128)
+        out["cpu_baseline"] = {"value": n_atoms * len(idx) / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"{len(idx)} of {n_s} grid points (seeded), all {n_atoms} atoms, {dt:.1f} s"}
+        out["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                           "points": int(len(idx)), "tolerance": 1e-4}
+    if args.paths and rank == 0:
+        out["paths"] = measure_paths(args, dev)
+    plan.check()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def measure_paths(args, dev):
+    """Other rows of the hot path on their own workloads (device time)."""
+    import torch
+    from paper_1010_2641_gb300 import api
+    from paper_1010_2641_gb300 import workloads as W
+    res = {}
+    # plain FP64 kernel on a 1/64 slice of the sphere map (every 64th l-plane pair)
+    c, axes = workload()
+    sub = [axes[0], axes[1], axes[2][::16]]
+    n_s = len(sub[0]) * len(sub[1]) * len(sub[2])
+    for path in ("fp64", "generic"):
+        plan = api.Plan(c.coef, W.LATTICE_A, len(c.xyz), axes=sub, atom_species=c.species, path=path, timing=True)
+        xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
+        plan.amplitude(xyz)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2):
+            plan.amplitude(xyz)
+            ms.append(plan.timing()[0])
+        res[f"{path}_sphere_sub"] = {"value": len(c.xyz) * n_s / (np.mean(ms) * 1e-3), "unit": UNIT,
+                                     "n_s": n_s, "kernel_ms": float(np.mean(ms))}
+    # adjoint on the strained cube (102,400 atoms x 128^3)
+    cube = W.strained_cube()
+    ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
+          W.linspace_axis(4.0, 128, step=0.005)]
+    plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, timing=True)
+    x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
+    I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
+    A = plan.amplitude(x)
+    plan.backward(x, A, I_obs)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(2):
+        plan.backward(x, A, I_obs)
+        ms.append(plan.timing()[0])
+    res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (np.mean(ms) * 1e-3), "unit": UNIT,
+                           "kernel_ms": float(np.mean(ms))}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--paths", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

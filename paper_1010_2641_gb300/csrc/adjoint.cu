@@ -1,0 +1,351 @@
+// Loss and adjoint of Eq. 2 with respect to the atom positions.
+//
+//   L        = sum_S (|A(S)|^2 - I_obs(S))^2
+//   g(S)     = 4 (|A|^2 - I_obs) conj(A)        (or conj(G) for a general VJP)
+//   dL/dr_j  = -2 pi w_j sum_S S Im( g(S) f_s(|S|) exp(2 i pi S.r_j) )
+//
+// With the forward's split S.r_j = s.t + c_j + s.x'_j (mod 1) the factor
+// exp(2 i pi s.t) and f_s(|S|) are folded into one weight per (species, S):
+//   gF_s(S) = g(S) f_s(|S|) exp(2 i pi s.t)
+// so the per-pair work is the forward's phase + MUFU sincos plus
+//   v = Im(gF e^{2 i pi phi}) = gF.re sin + gF.im cos,   acc_d += S_d v.
+//
+// k_loss_weights  O(M): L partials (FP64, fixed grid, fixed order), the
+//                 expanded S table {s, gF.re | S, gF.im} per species.
+// k_adjoint       atom-parallel (the paper's alternative decomposition,
+//                 Section 2.2): each thread holds RA atoms in registers, S
+//                 tiles are staged in shared memory by the TMA engine; inner
+//                 sums per tile in FP32, outer sums in FP64 (the terms over
+//                 millions of S nearly cancel).  The exponentials are
+//                 recomputed, nothing of size N x M is stored.
+// k_adjoint_final sums the S-chunk partials in a fixed order, scales by
+//                 -2 pi w_j and writes the caller's atom order.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <vector>
+#include "device_common.cuh"
+#include "launch.h"
+
+namespace scatter {
+
+constexpr int kSTile = 256;        // S points per shared-memory stage
+constexpr int kAdjThreads = 128;
+constexpr int kAdjRA = 8;          // atoms per thread
+constexpr int kLossThreads = 256;
+
+struct LossArgs {
+  const float2* A;        // forward amplitude (loss mode) or null
+  const float* I_obs;
+  const float2* G;        // upstream gradient (vjp mode) or null
+  int64_t n_s;
+  int grid;
+  const double* S64;
+  const double* axis64;
+  int64_t n0, n1, n2;
+  double H[3];
+  const double* shift;
+  const float* coef;
+  int n_species;
+  float inv4a2;
+  float4* table;          // [n_species][M][2]
+  double* loss_part;      // [gridDim.x]
+};
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a) {
+  double lpart = 0.0;
+  const double* t = a.shift;
+  const bool shifted = t[0] != 0.0 || t[1] != 0.0 || t[2] != 0.0;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < a.n_s;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    double S[3];
+    if (a.grid) {
+      const int64_t i2 = m % a.n2, line = m / a.n2, i1 = line % a.n1, i0 = line / a.n1;
+      S[0] = a.axis64[i0];
+      S[1] = a.axis64[a.n0 + i1];
+      S[2] = a.axis64[a.n0 + a.n1 + i2];
+    } else {
+      S[0] = a.S64[3 * m];
+      S[1] = a.S64[3 * m + 1];
+      S[2] = a.S64[3 * m + 2];
+    }
+    float2 g;
+    if (a.A) {
+      const float2 A = a.A[m];
+      const double I = (double)A.x * A.x + (double)A.y * A.y;
+      const double d = I - (double)a.I_obs[m];
+      lpart += d * d;
+      g = make_float2((float)(4.0 * d * A.x), (float)(-4.0 * d * A.y));
+    } else {
+      const float2 G = a.G[m];
+      g = make_float2(G.x, -G.y);
+    }
+    const float2 ph = shifted ? dev::shift_phase(S[0] - a.H[0], S[1] - a.H[1], S[2] - a.H[2], t)
+                              : make_float2(1.f, 0.f);
+    const float2 gp = dev::cmul(g, ph);
+    const float Sx = (float)S[0], Sy = (float)S[1], Sz = (float)S[2];
+    const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
+    const float sx = (float)(S[0] - a.H[0]), sy = (float)(S[1] - a.H[1]), sz = (float)(S[2] - a.H[2]);
+    for (int sp = 0; sp < a.n_species; ++sp) {
+      const float2 gF = dev::cmul(gp, dev::form_factor(a.coef + kNCoef * sp, s2));
+      float4* row = a.table + 2 * ((int64_t)sp * a.n_s + m);
+      row[0] = make_float4(sx, sy, sz, gF.x);
+      row[1] = make_float4(Sx, Sy, Sz, gF.y);
+    }
+  }
+  // deterministic block reduction of the misfit
+  __shared__ double sh[kLossThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lpart;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kLossThreads / 32; ++w) v += sh[w];
+    a.loss_part[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_loss_final(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < n; ++i) v += part[i];
+    *out = v;
+  }
+}
+
+struct AdjArgs {
+  const float4* atom4;
+  const AdjBlock* blocks;
+  const float4* table;     // [n_species][M][2]
+  int64_t n_s;
+  int64_t s_per_chunk;
+  float* partial;          // [split][n_slots][3]
+  int64_t n_slots;
+  unsigned* status;
+};
+
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
+  __shared__ __align__(128) float4 sh_s[2][kSTile * 2];
+  __shared__ __align__(8) uint64_t sh_bar[2];
+  const int tid = threadIdx.x;
+  const AdjBlock blk = a.blocks[blockIdx.x];
+  const int chunk = blockIdx.y;
+  const int64_t m0 = (int64_t)chunk * a.s_per_chunk;
+  const int64_t m1 = dev::min64(a.n_s, m0 + a.s_per_chunk);
+  const float4* tab = a.table + 2 * (int64_t)blk.species * a.n_s;
+
+  float x[kAdjRA], y[kAdjRA], z[kAdjRA], c[kAdjRA];
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) {
+    const int i = r * kAdjThreads + tid;
+    const float4 at = i < blk.count ? a.atom4[blk.begin + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    x[r] = at.x;
+    y[r] = at.y;
+    z[r] = at.z;
+    c[r] = at.w;
+  }
+  double gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) gx[r] = gy[r] = gz[r] = 0.0;
+
+  if (tid == 0) {
+    dev::mbar_init(&sh_bar[0], 1);
+    dev::mbar_init(&sh_bar[1], 1);
+    dev::mbar_fence_init();
+  }
+  __syncthreads();
+  const int64_t n_tiles = m1 > m0 ? (m1 - m0 + kSTile - 1) / kSTile : 0;
+  auto issue = [&](int64_t k) {
+    if (k >= n_tiles) return;
+    const int64_t b = m0 + k * kSTile;
+    const int cnt = (int)dev::min64(kSTile, m1 - b);
+    const int st = (int)(k & 1);
+    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * 32u);
+    dev::bulk_g2s(&sh_s[st][0], tab + 2 * b, (uint32_t)cnt * 32u, &sh_bar[st]);
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  bool aborted = false;
+  for (int64_t k = 0; k < n_tiles; ++k) {
+    const int st = (int)(k & 1);
+    const int cnt = (int)dev::min64(kSTile, m1 - (m0 + k * kSTile));
+    const bool ok = dev::mbar_wait_bounded(&sh_bar[st], (uint32_t)((k >> 1) & 1));
+    float ax[kAdjRA], ay[kAdjRA], az[kAdjRA];
+#pragma unroll
+    for (int r = 0; r < kAdjRA; ++r) ax[r] = ay[r] = az[r] = 0.f;
+    if (ok) {
+      const float4* sv = sh_s[st];
+#pragma unroll 2
+      for (int j = 0; j < cnt; ++j) {
+        const float4 p = sv[2 * j];      // s, gF.re
+        const float4 q = sv[2 * j + 1];  // S, gF.im
+#pragma unroll
+        for (int r = 0; r < kAdjRA; ++r) {
+          const float f = dev::frac_rn(fmaf(p.z, z[r], fmaf(p.y, y[r], fmaf(p.x, x[r], c[r]))));
+          float sn, cs;
+          dev::sincos_cycles_mufu(f, &sn, &cs);
+          const float v = fmaf(p.w, sn, q.w * cs);
+          ax[r] = fmaf(q.x, v, ax[r]);
+          ay[r] = fmaf(q.y, v, ay[r]);
+          az[r] = fmaf(q.z, v, az[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kAdjRA; ++r) {
+      gx[r] += ax[r];
+      gy[r] += ay[r];
+      gz[r] += az[r];
+    }
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      if (tid == 0) {
+        dev::set_status(a.status, kStatusTimeout);
+        for (int64_t kk = k; kk < dev::min64(k + 2, n_tiles); ++kk)
+          dev::mbar_wait_bounded(&sh_bar[kk & 1], (uint32_t)((kk >> 1) & 1), 1LL << 28);
+      }
+      break;
+    }
+    if (tid == 0) issue(k + 2);
+  }
+  if (aborted) return;
+  float* out = a.partial + (int64_t)chunk * a.n_slots * 3;
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) {
+    const int i = r * kAdjThreads + tid;
+    if (i < blk.count) {
+      const int64_t slot = blk.begin + i;
+      out[3 * slot] = (float)gx[r];
+      out[3 * slot + 1] = (float)gy[r];
+      out[3 * slot + 2] = (float)gz[r];
+    }
+  }
+}
+
+__global__ void k_adjoint_final(const float* partial, int split, int64_t n_slots, const int32_t* slot_src,
+                                const float* atom_w, float* grad) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= n_slots) return;
+  const int32_t src = slot_src[slot];
+  if (src < 0) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < split; ++c)
+    for (int d = 0; d < 3; ++d) v[d] += (double)partial[((int64_t)c * n_slots + slot) * 3 + d];
+  const double scale = -2.0 * 3.14159265358979323846 * (double)atom_w[slot];
+  for (int d = 0; d < 3; ++d) grad[3 * (int64_t)src + d] = (float)(scale * v[d]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+scatter_status prepare_adjoint(scatter_plan_s* p) {
+  if (p->adj_ready) return SCATTER_OK;
+  if (p->batch != 1) return fail(SCATTER_ERR_UNSUPPORTED, "backward is available for single instances");
+  std::vector<AdjBlock> blocks;
+  const int per = kAdjThreads * kAdjRA;
+  for (const Segment& s : p->all_segs)
+    for (int64_t b = s.begin; b < s.end; b += per)
+      blocks.push_back(AdjBlock{b, (int32_t)dev::min64(per, s.end - b), s.species});
+  // split over S so that the grid fills the GPU a few times over
+  int bps = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_adjoint, kAdjThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    bps = 1;
+  }
+  const int64_t nb = std::max<int64_t>(1, (int64_t)blocks.size());
+  const int64_t target = 4LL * p->n_sm * std::max(1, bps);
+  int64_t split = std::max<int64_t>(1, (target + nb - 1) / nb);
+  int64_t s_per = (p->n_s + split - 1) / split;
+  s_per = std::max<int64_t>(kSTile, (s_per + kSTile - 1) / kSTile * kSTile);
+  split = std::max<int64_t>(1, (p->n_s + s_per - 1) / s_per);
+  p->adj_split = (int)split;
+  p->adj_s_per_chunk = s_per;
+  p->adj_blocks = (int)blocks.size();
+  cudaError_t e;
+  const size_t tab_bytes = (size_t)p->n_species * (size_t)p->n_s * 2 * sizeof(float4);
+  const size_t part_bytes = (size_t)split * (size_t)p->n_slots * 3 * sizeof(float);
+  if (!blocks.empty()) {
+    if ((e = cudaMalloc(&p->d.adj_blocks, blocks.size() * sizeof(AdjBlock))) != cudaSuccess)
+      return cuda_status(e, "cudaMalloc");
+    if ((e = cudaMemcpy(p->d.adj_blocks, blocks.data(), blocks.size() * sizeof(AdjBlock), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return cuda_status(e, "cudaMemcpy");
+  }
+  if (tab_bytes && (e = cudaMalloc(&p->d.adj_table, tab_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  if (part_bytes && (e = cudaMalloc(&p->d.adj_partial, part_bytes)) != cudaSuccess)
+    return cuda_status(e, "cudaMalloc");
+  p->base_bytes += (int64_t)(tab_bytes + part_bytes + blocks.size() * sizeof(AdjBlock));
+  p->adj_ready = true;
+  return SCATTER_OK;
+}
+
+scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float* occ, const float2* A,
+                               const float* I_obs, const float2* G, double* loss_out, float* grad,
+                               cudaStream_t st) {
+  if (p->path == SCATTER_PATH_FP64_REF)
+    return fail(SCATTER_ERR_UNSUPPORTED, "backward runs on the generic path; plan with SCATTER_PATH_GENERIC");
+  scatter_status s = SCATTER_OK;
+  if (grad) {
+    if ((s = prepare_adjoint(p)) != SCATTER_OK) return s;
+    // positions (and the centring t) exactly as the forward used them
+    if ((s = launch_prep(p, xyz, occ, st)) != SCATTER_OK) return s;
+  } else if (p->n_s > 0 && p->n_atoms > 0) {
+    // loss only: the shift is not needed, but the table write is skipped too
+  }
+  if (p->n_s == 0) {
+    if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(double), st);
+    if (grad && p->n_atoms) cudaMemsetAsync(grad, 0, sizeof(float) * 3 * p->n_atoms, st);
+    return cuda_status(cudaGetLastError(), "backward (empty)");
+  }
+  LossArgs la{};
+  la.A = A;
+  la.I_obs = I_obs;
+  la.G = G;
+  la.n_s = p->n_s;
+  la.grid = p->s_kind == SCATTER_S_GRID;
+  la.S64 = p->d.S64;
+  la.axis64 = p->d.axis64;
+  la.n0 = p->n_axis[0];
+  la.n1 = p->n_axis[1];
+  la.n2 = p->n_axis[2];
+  for (int d = 0; d < 3; ++d) la.H[d] = p->inst[0].H[d];
+  la.shift = p->d.inst_shift;
+  la.coef = p->d.coef;
+  la.n_species = grad ? p->n_species : 0;
+  la.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
+  la.table = p->d.adj_table;
+  la.loss_part = p->d.loss_part;
+  k_loss_weights<<<kLossParts, kLossThreads, 0, st>>>(la);
+  p->last_launches += 1;
+  if (A && loss_out) {
+    k_loss_final<<<1, 32, 0, st>>>(p->d.loss_part, kLossParts, loss_out);
+    p->last_launches += 1;
+  }
+  if (grad && p->n_atoms > 0) {
+    AdjArgs aa{};
+    aa.atom4 = p->d.atom4;
+    aa.blocks = p->d.adj_blocks;
+    aa.table = p->d.adj_table;
+    aa.n_s = p->n_s;
+    aa.s_per_chunk = p->adj_s_per_chunk;
+    aa.partial = p->d.adj_partial;
+    aa.n_slots = p->n_slots;
+    aa.status = p->d.status;
+    if (p->adj_blocks > 0) {
+      dim3 gridd((unsigned)p->adj_blocks, (unsigned)p->adj_split);
+      timing_begin(p, st);
+      k_adjoint<<<gridd, kAdjThreads, 0, st>>>(aa);
+      timing_end(p, st);
+      p->last_launches += 1;
+    }
+    const int64_t nb = (p->n_slots + 255) / 256;
+    k_adjoint_final<<<(unsigned)nb, 256, 0, st>>>(p->d.adj_partial, p->adj_split, p->n_slots, p->d.slot_src,
+                                                  p->d.atom_w, grad);
+    p->last_launches += 1;
+  }
+  return cuda_status(cudaGetLastError(), "backward launch");
+}
+
+}  // namespace scatter

@@ -1,0 +1,192 @@
+// Entry points of libscatter that run on a plan: amplitude, intensity,
+// backward / vjp, status check, error model and plan info.
+#include <cmath>
+#include <cstring>
+#include "launch.h"
+#include "plan.h"
+
+using namespace scatter;
+
+namespace {
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// A device (or managed) pointer of the plan's device; NULL only if allowed.
+scatter_status check_ptr(const void* ptr, int device, const char* name, bool allow_null) {
+  if (!ptr) {
+    if (allow_null) return SCATTER_OK;
+    return fail(SCATTER_ERR_INVALID_ARG, "%s is NULL", name);
+  }
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SCATTER_ERR_INVALID_ARG, "%s is not a CUDA pointer", name);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(SCATTER_ERR_INVALID_ARG, "%s must be device memory", name);
+  if (at.device != device)
+    return fail(SCATTER_ERR_INVALID_ARG, "%s lives on device %d, the plan on device %d", name, at.device, device);
+  return SCATTER_OK;
+}
+
+scatter_status check_inputs(scatter_plan_t p, const double* xyz, const float* occ) {
+  if (!p) return fail(SCATTER_ERR_INVALID_ARG, "plan is NULL");
+  scatter_status st = check_ptr(xyz, p->device, "xyz", p->n_atoms == 0);
+  if (st == SCATTER_OK) st = check_ptr(occ, p->device, "occ", true);
+  return st;
+}
+
+scatter_status forward(scatter_plan_t p, const double* xyz, const float* occ, float2* amp, float* inten,
+                       cudaStream_t st) {
+  p->last_launches = 0;
+  if (p->n_s == 0) return SCATTER_OK;
+  if (p->path == SCATTER_PATH_FP64_REF) return launch_f64(p, xyz, occ, amp, inten, st);
+  scatter_status s = launch_prep(p, xyz, occ, st);
+  if (s != SCATTER_OK) return s;
+  return launch_generic(p, amp, inten, st);
+}
+
+}  // namespace
+
+extern "C" scatter_status scatter_amplitude(scatter_plan_t p, const double* xyz, const float* occ, void* A_out,
+                                            void* stream) {
+  scatter_status st = check_inputs(p, xyz, occ);
+  if (st != SCATTER_OK) return st;
+  if ((st = check_ptr(A_out, p->device, "A_out", p->n_s == 0)) != SCATTER_OK) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  return forward(p, xyz, occ, static_cast<float2*>(A_out), nullptr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" scatter_status scatter_intensity(scatter_plan_t p, const double* xyz, const float* occ, float* I_out,
+                                            void* stream) {
+  scatter_status st = check_inputs(p, xyz, occ);
+  if (st != SCATTER_OK) return st;
+  if ((st = check_ptr(I_out, p->device, "I_out", p->n_s == 0)) != SCATTER_OK) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  return forward(p, xyz, occ, nullptr, I_out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" scatter_status scatter_backward(scatter_plan_t p, const double* xyz, const float* occ, const void* A,
+                                           const float* I_obs, double* loss_out, float* dL_dxyz, void* stream) {
+  scatter_status st = check_inputs(p, xyz, occ);
+  if (st != SCATTER_OK) return st;
+  if ((st = check_ptr(A, p->device, "A", p->n_s == 0)) != SCATTER_OK) return st;
+  if ((st = check_ptr(I_obs, p->device, "I_obs", p->n_s == 0)) != SCATTER_OK) return st;
+  if ((st = check_ptr(loss_out, p->device, "loss_out", true)) != SCATTER_OK) return st;
+  if ((st = check_ptr(dL_dxyz, p->device, "dL_dxyz", true)) != SCATTER_OK) return st;
+  if (p->s_kind == SCATTER_S_GID_GRID) return fail(SCATTER_ERR_UNSUPPORTED, "no backward for GID grids");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  p->last_launches = 0;
+  return launch_backward(p, xyz, occ, static_cast<const float2*>(A), I_obs, nullptr, loss_out, dL_dxyz,
+                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" scatter_status scatter_vjp(scatter_plan_t p, const double* xyz, const float* occ, const void* G,
+                                      float* dL_dxyz, void* stream) {
+  scatter_status st = check_inputs(p, xyz, occ);
+  if (st != SCATTER_OK) return st;
+  if ((st = check_ptr(G, p->device, "G", p->n_s == 0)) != SCATTER_OK) return st;
+  if ((st = check_ptr(dL_dxyz, p->device, "dL_dxyz", p->n_atoms == 0)) != SCATTER_OK) return st;
+  if (p->s_kind == SCATTER_S_GID_GRID) return fail(SCATTER_ERR_UNSUPPORTED, "no vjp for GID grids");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  p->last_launches = 0;
+  return launch_backward(p, xyz, occ, nullptr, nullptr, static_cast<const float2*>(G), nullptr, dL_dxyz,
+                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" scatter_status scatter_check(scatter_plan_t p, void* stream) {
+  if (!p) return fail(SCATTER_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "stream synchronize");
+  unsigned word = 0;
+  if ((e = cudaMemcpy(&word, p->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_status(e, "status read");
+  if (word) {
+    const unsigned zero = 0;
+    cudaMemcpy(p->d.status, &zero, sizeof(unsigned), cudaMemcpyHostToDevice);
+  }
+  if (word & kStatusTimeout) return fail(SCATTER_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (word & kStatusNonFinite) return fail(SCATTER_ERR_NUMERIC, "non-finite position or occupancy");
+  return SCATTER_OK;
+}
+
+extern "C" scatter_status scatter_error_bound(scatter_plan_t p, double radius, double* per_pair,
+                                              double* rel_l2_random) {
+  if (!p || !per_pair || !rel_l2_random || !(radius >= 0) || !std::isfinite(radius))
+    return fail(SCATTER_ERR_INVALID_ARG, "bad argument");
+  const double u = std::ldexp(1.0, -24);  // fp32 unit roundoff
+  const double pi = 3.14159265358979323846;
+  if (p->path == SCATTER_PATH_FP64_REF) {
+    // FP64 phases |S.r| <= |S| (radius + |t|): bounded by the output rounding
+    *per_pair = u;
+    *rel_l2_random = u;
+    return SCATTER_OK;
+  }
+  const double sr = (p->s_max[0] + p->s_max[1] + p->s_max[2]) * radius;  // |s . x'|
+  const double phi = 0.5 + sr;                                           // |c + s . x'|
+  // phase error in cycles: stored s and x' (2 u sr), stored c (u/2), three
+  // FMA roundings (3 u phi), 2 pi scaling of the reduced phase (u/2)
+  const double dphi = 2.0 * u * sr + 0.5 * u + 3.0 * u * phi + 0.5 * u;
+  const double mufu = std::ldexp(1.0, -20);  // sin.approx/cos.approx absolute error bound
+  *per_pair = 2.0 * pi * dphi + std::sqrt(2.0) * mufu;
+  // blocked FP32 accumulation: tiles of 256 atoms, then tiles summed
+  const double per_seg = (double)std::max<int64_t>(p->n_slots, 1) / 256.0;
+  const double acc = u * std::sqrt(256.0 + per_seg + (double)p->tiling.split_k);
+  *rel_l2_random = *per_pair + acc;
+  return SCATTER_OK;
+}
+
+extern "C" scatter_status scatter_plan_get_info(scatter_plan_t p, scatter_plan_info* info) {
+  if (!p || !info) return fail(SCATTER_ERR_INVALID_ARG, "bad argument");
+  std::memset(info, 0, sizeof(*info));
+  info->path = p->path;
+  info->threads = p->tiling.threads;
+  info->points_per_thread = p->tiling.R;
+  info->split_k = p->tiling.split_k;
+  info->n_sm = p->n_sm;
+  info->n_atoms_padded = p->n_slots;
+  info->n_s = p->n_s;
+  info->workspace_bytes = p->base_bytes + p->tiling_bytes;
+  for (int d = 0; d < 3; ++d) info->center_hkl[d] = p->inst.empty() ? 0.0 : p->inst[0].H[d];
+  if (!p->inst.empty()) {
+    double t[3] = {0, 0, 0};
+    cudaMemcpy(t, p->d.inst_shift, sizeof(t), cudaMemcpyDeviceToHost);
+    for (int d = 0; d < 3; ++d) info->shift[d] = t[d];
+  }
+  return SCATTER_OK;
+}
+
+extern "C" scatter_status scatter_plan_timing(scatter_plan_t p, double* ms_main, int32_t* kernel_launches) {
+  if (!p || !ms_main || !kernel_launches) return fail(SCATTER_ERR_INVALID_ARG, "bad argument");
+  *kernel_launches = p->last_launches;
+  *ms_main = 0.0;
+  if (!p->timing || !p->timed_call) return fail(SCATTER_ERR_UNSUPPORTED, "timing not enabled or no call made");
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaEventSynchronize(p->ev_end);
+  if (e != cudaSuccess) return cuda_status(e, "event synchronize");
+  float ms = 0.f;
+  if ((e = cudaEventElapsedTime(&ms, p->ev_begin, p->ev_end)) != cudaSuccess) return cuda_status(e, "elapsed time");
+  *ms_main = ms;
+  return SCATTER_OK;
+}

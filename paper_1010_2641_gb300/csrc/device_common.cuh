@@ -1,0 +1,127 @@
+// Device helpers shared by the scattering kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "plan.h"
+
+namespace scatter {
+namespace dev {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// Phase arithmetic
+// ---------------------------------------------------------------------------
+
+// x - rint(x) for |x| < 2^22, exactly, on the FMA pipe.  (cvt.rni runs on a
+// 16/clk/SM pipe on this GPU, the same rate as the MUFU sin/cos the kernels
+// are bound by, so it is avoided in the inner loops.)  The add/sub of
+// 1.5 * 2^23 rounds x to an integer in round-to-nearest-even.
+__device__ __forceinline__ float frac_rn(float x) {
+  const float kMagic = 12582912.0f;  // 1.5 * 2^23
+  const float n = __fsub_rn(__fadd_rn(x, kMagic), kMagic);
+  return __fsub_rn(x, n);
+}
+
+// sin and cos of 2*pi*f for |f| <= 1/2 (cycles) on the MUFU pipe
+// (sin.approx/cos.approx: absolute error below 1e-6 on [-pi, pi]).
+__device__ __forceinline__ void sincos_cycles_mufu(float f, float* s, float* c) {
+  const float kTwoPi = 6.28318530717958647692f;
+  const float th = __fmul_rn(f, kTwoPi);
+  *s = __sinf(th);
+  *c = __cosf(th);
+}
+
+// ---------------------------------------------------------------------------
+// Scattering factor (Section 3, pynx.fthomson form; Section 4.2 f', f'', DW)
+//   f(s) = (sum_i a_i exp(-b_i s^2) + c + f' + i f'') exp(-B s^2),
+// evaluated in FP32 with s^2 = |S|^2 / (4 a^2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 form_factor(const float* __restrict__ cf, float s2) {
+  float f0 = __ldg(cf + 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) f0 = fmaf(__ldg(cf + i), __expf(-__ldg(cf + 4 + i) * s2), f0);
+  const float dw = __expf(-__ldg(cf + 11) * s2);
+  return make_float2((f0 + __ldg(cf + 9)) * dw, __ldg(cf + 10) * dw);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// e^{2 pi i s.t} for the integer centring t, reduced in FP64 (O(M) work).
+__device__ __forceinline__ float2 shift_phase(double s0, double s1, double s2, const double* t) {
+  const double ph = s0 * t[0] + s1 * t[1] + s2 * t[2];
+  const float f = (float)(ph - rint(ph));
+  float sn, cs;
+  sincospif(2.0f * f, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (TMA engine) with bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of `bar` to complete, giving up after roughly
+// `budget_cycles` SM clocks.  Returns false on timeout (the caller records
+// kStatusTimeout and leaves the loop).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget_cycles = (1LL << 31)) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget_cycles) return false;
+  }
+  return true;
+}
+
+// 1-D bulk copy global -> shared through the TMA engine; completion is
+// signalled on `bar` as transaction bytes.  dst, src and bytes must be
+// multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
+  if (status) atomicOr(status, bit);
+}
+
+}  // namespace dev
+}  // namespace scatter

@@ -1,0 +1,43 @@
+// Host-side launch functions shared between translation units of libscatter.
+#pragma once
+
+#include "plan.h"
+
+namespace scatter {
+
+// Per-call position preparation (all instances): integer centring t of each
+// instance (rint of its bounding-box centre), split r - t = n + delta,
+// c = frac(H . delta), fp32 slots.  Enqueued on `st`.
+scatter_status launch_prep(scatter_plan_t p, const double* xyz, const float* occ, cudaStream_t st);
+
+// A(S) (and/or |A|^2) of every point with the generic FP32/MUFU kernel;
+// positions must have been prepared by launch_prep on the same stream.
+scatter_status launch_generic(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
+
+// Plain FP64 kernel (no prep needed).
+scatter_status launch_f64(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
+                          float* int_out, cudaStream_t st);
+
+// Loss L (loss_out), and/or gradient dL/dr (grad, caller order) from either
+// (A, I_obs) [misfit] or an upstream gradient G [vjp].  Runs prep itself.
+scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float* occ, const float2* A,
+                               const float* I_obs, const float2* G, double* loss_out, float* grad,
+                               cudaStream_t st);
+
+// Opt-in event timing around the main kernel of a call.
+inline void timing_begin(scatter_plan_s* p, cudaStream_t st) {
+  if (p->timing) cudaEventRecord(p->ev_begin, st);
+}
+inline void timing_end(scatter_plan_s* p, cudaStream_t st) {
+  if (p->timing) {
+    cudaEventRecord(p->ev_end, st);
+    p->timed_call = true;
+  }
+}
+
+// Occupancy-based residency of the generic kernel for a tiling.
+int generic_blocks_per_sm(const scatter_plan_s* p, const Tiling& t);
+bool generic_tiling_supported(const Tiling& t);
+int64_t generic_num_tiles(const scatter_plan_s* p, const Tiling& t);
+
+}  // namespace scatter

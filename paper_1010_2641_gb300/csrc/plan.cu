@@ -1,0 +1,432 @@
+// scatter_plan / scatter_plan_destroy: everything that does not depend on
+// atom positions (Eq. 2 factored per species, Section 4.2; the atom list cut
+// into chunks, the modern form of the paper's atom batching, Section 5).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <vector>
+#include "launch.h"
+#include "plan.h"
+#include "tuner.h"
+
+using scatter::fail;
+
+namespace scatter {
+namespace {
+
+bool finite_all(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+bool is_integer(double v) { return std::isfinite(v) && std::fabs(v - std::rint(v)) < 1e-12; }
+
+template <class T>
+scatter_status upload(T** dst, const T* src, size_t n, int64_t* bytes) {
+  *dst = nullptr;
+  if (n == 0) return SCATTER_OK;
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  *bytes += (int64_t)(n * sizeof(T));
+  if (src) {
+    e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemcpy");
+  }
+  return SCATTER_OK;
+}
+
+template <class T>
+void release(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
+  if (!pr) return fail(SCATTER_ERR_INVALID_ARG, "problem is NULL");
+  if (pr->n_atoms < 0 || pr->n_atoms > (int64_t)INT32_MAX)
+    return fail(SCATTER_ERR_INVALID_ARG, "n_atoms out of range (%lld)", (long long)pr->n_atoms);
+  if (pr->n_species < 1 || pr->n_species > kMaxSpecies)
+    return fail(SCATTER_ERR_INVALID_ARG, "n_species must be in [1, %d]", kMaxSpecies);
+  if (!pr->species) return fail(SCATTER_ERR_INVALID_ARG, "species is NULL");
+  for (int s = 0; s < pr->n_species; ++s) {
+    const scatter_species& sp = pr->species[s];
+    if (!finite_all(sp.a, 4) || !finite_all(sp.b, 4) || !std::isfinite(sp.c) || !std::isfinite(sp.fp) ||
+        !std::isfinite(sp.fpp) || !std::isfinite(sp.b_dw))
+      return fail(SCATTER_ERR_INVALID_ARG, "species %d has non-finite coefficients", s);
+  }
+  if (pr->atom_species) {
+    for (int64_t j = 0; j < pr->n_atoms; ++j)
+      if (pr->atom_species[j] < 0 || pr->atom_species[j] >= pr->n_species)
+        return fail(SCATTER_ERR_INVALID_ARG, "atom %lld has species %d outside [0, %d)", (long long)j,
+                    pr->atom_species[j], pr->n_species);
+  }
+  if (!(pr->lattice_a > 0) || !std::isfinite(pr->lattice_a))
+    return fail(SCATTER_ERR_INVALID_ARG, "lattice_a must be positive and finite");
+  if (pr->s_kind < SCATTER_S_LIST || pr->s_kind > SCATTER_S_GID_GRID)
+    return fail(SCATTER_ERR_INVALID_ARG, "unknown s_kind %d", pr->s_kind);
+  if (pr->s_kind == SCATTER_S_LIST) {
+    if (pr->n_s < 0) return fail(SCATTER_ERR_INVALID_ARG, "n_s < 0");
+    if (pr->n_s > 0 && !pr->s_list) return fail(SCATTER_ERR_INVALID_ARG, "s_list is NULL");
+    if (pr->n_s > 0 && !finite_all(pr->s_list, 3 * pr->n_s))
+      return fail(SCATTER_ERR_INVALID_ARG, "s_list has non-finite values");
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      if (pr->n_axis[d] < 1) return fail(SCATTER_ERR_INVALID_ARG, "n_axis[%d] < 1", d);
+      if (!pr->axis[d]) return fail(SCATTER_ERR_INVALID_ARG, "axis[%d] is NULL", d);
+      if (!finite_all(pr->axis[d], pr->n_axis[d]))
+        return fail(SCATTER_ERR_INVALID_ARG, "axis[%d] has non-finite values", d);
+    }
+    const double m = (double)pr->n_axis[0] * pr->n_axis[1] * pr->n_axis[2];
+    if (m > 4e9) return fail(SCATTER_ERR_INVALID_ARG, "grid has too many points");
+  }
+  if (pr->s_kind == SCATTER_S_GID_GRID) {
+    if (!(pr->wavelength > 0) || !std::isfinite(pr->wavelength))
+      return fail(SCATTER_ERR_INVALID_ARG, "wavelength must be positive");
+    if (!std::isfinite(pr->alpha_i) || !std::isfinite(pr->delta) || !std::isfinite(pr->beta) ||
+        pr->delta < 0 || pr->beta < 0)
+      return fail(SCATTER_ERR_INVALID_ARG, "invalid alpha_i/delta/beta");
+  }
+  if (pr->center_mode != 0 && pr->center_mode != 1)
+    return fail(SCATTER_ERR_INVALID_ARG, "center_mode must be 0 or 1");
+  if (pr->center_mode == 1)
+    for (int d = 0; d < 3; ++d)
+      if (!is_integer(pr->center_hkl[d]))
+        return fail(SCATTER_ERR_INVALID_ARG, "center_hkl must hold integers");
+  if (pr->batch < 1) return fail(SCATTER_ERR_INVALID_ARG, "batch < 1");
+  if (pr->batch > 1) {
+    if (pr->s_kind != SCATTER_S_LIST) return fail(SCATTER_ERR_INVALID_ARG, "batches need SCATTER_S_LIST");
+    if (!pr->atom_off || !pr->s_off) return fail(SCATTER_ERR_INVALID_ARG, "batch offsets are NULL");
+    if (pr->atom_off[0] != 0 || pr->s_off[0] != 0 || pr->atom_off[pr->batch] != pr->n_atoms ||
+        pr->s_off[pr->batch] != pr->n_s)
+      return fail(SCATTER_ERR_INVALID_ARG, "batch offsets must start at 0 and end at n_atoms / n_s");
+    for (int b = 0; b < pr->batch; ++b)
+      if (pr->atom_off[b + 1] < pr->atom_off[b] || pr->s_off[b + 1] < pr->s_off[b])
+        return fail(SCATTER_ERR_INVALID_ARG, "batch offsets must be non-decreasing");
+  }
+  if (op) {
+    if (op->path < SCATTER_PATH_AUTO || op->path > SCATTER_PATH_FP64_REF)
+      return fail(SCATTER_ERR_INVALID_ARG, "unknown path %d", op->path);
+    if (op->threads < 0 || op->points_per_thread < 0 || op->split_k < 0)
+      return fail(SCATTER_ERR_INVALID_ARG, "negative tile override");
+  }
+  return SCATTER_OK;
+}
+
+// Reference reflection H of one instance: rint of the mean S (or the given
+// center).  S - H is then small, which keeps s . x' small in FP32.
+void choose_H(const scatter_problem* pr, int64_t s_begin, int64_t s_end, double H[3]) {
+  if (pr->center_mode == 1) {
+    for (int d = 0; d < 3; ++d) H[d] = std::rint(pr->center_hkl[d]);
+    return;
+  }
+  for (int d = 0; d < 3; ++d) {
+    double sum = 0.0;
+    int64_t n = 0;
+    if (pr->s_kind == SCATTER_S_LIST) {
+      for (int64_t m = s_begin; m < s_end; ++m) sum += pr->s_list[3 * m + d];
+      n = s_end - s_begin;
+    } else if (pr->s_kind == SCATTER_S_GRID || d < 2) {
+      for (int64_t i = 0; i < pr->n_axis[d]; ++i) sum += pr->axis[d][i];
+      n = pr->n_axis[d];
+    }
+    H[d] = n > 0 ? std::rint(sum / (double)n) : 0.0;
+  }
+}
+
+// Splits each instance's slot range into `split_k` contiguous chunks and cuts
+// every chunk at species boundaries into segments.
+void build_chunks(scatter_plan_s* p, int split_k) {
+  p->segs.clear();
+  p->chunk_seg_off.assign(1, 0);
+  p->chunk_slots.clear();
+  for (size_t b = 0; b < p->inst.size(); ++b) {
+    const Instance& in = p->inst[b];
+    // species segments of this instance
+    std::vector<Segment> sp;
+    for (const Segment& s : p->all_segs)
+      if (s.instance == (int32_t)b) sp.push_back(s);
+    const int64_t n = in.slot_end - in.slot_begin;
+    int64_t per = (n + split_k - 1) / split_k;
+    per = (per + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+    if (per == 0) per = kSlotAlign;
+    for (int c = 0; c < split_k; ++c) {
+      const int64_t lo = in.slot_begin + c * per, hi = std::min(in.slot_end, lo + per);
+      int64_t cnt = 0;
+      for (const Segment& s : sp) {
+        const int64_t b2 = std::max(lo, s.begin), e2 = std::min(hi, s.end);
+        if (b2 < e2) {
+          p->segs.push_back(Segment{b2, e2, s.species, s.instance});
+          cnt += e2 - b2;
+        }
+      }
+      p->chunk_seg_off.push_back((int32_t)p->segs.size());
+      p->chunk_slots.push_back(cnt);
+    }
+  }
+}
+
+}  // namespace
+
+scatter_status apply_tiling(scatter_plan_s* p, const Tiling& t) {
+  if (!generic_tiling_supported(t)) return fail(SCATTER_ERR_INVALID_ARG, "unsupported tiling");
+  p->tiling = t;
+  build_chunks(p, t.split_k);
+  release(p->d.segs);
+  release(p->d.chunk_seg_off);
+  release(p->d.partial);
+  int64_t bytes = 0;
+  scatter_status st = upload(&p->d.segs, p->segs.data(), p->segs.size(), &bytes);
+  if (st == SCATTER_OK) st = upload(&p->d.chunk_seg_off, p->chunk_seg_off.data(), p->chunk_seg_off.size(), &bytes);
+  const int n_chunks_per_inst = t.split_k;
+  if (st == SCATTER_OK && n_chunks_per_inst > 1 && p->n_s > 0)
+    st = upload<float2>(&p->d.partial, nullptr, (size_t)n_chunks_per_inst * (size_t)p->n_s, &bytes);
+  p->tiling_bytes = bytes;
+  return st;
+}
+
+}  // namespace scatter
+
+using namespace scatter;
+
+extern "C" void scatter_plan_destroy(scatter_plan_t p) {
+  if (!p) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  DeviceBuffers& d = p->d;
+  release(d.slot_src);
+  release(d.slot_inst);
+  release(d.atom4);
+  release(d.atom_w);
+  release(d.atom_species);
+  release(d.segs);
+  release(d.chunk_seg_off);
+  release(d.coef);
+  release(d.coef64);
+  release(d.atom_off);
+  release(d.inst_slot_begin);
+  release(d.inst_H);
+  release(d.inst_shift);
+  release(d.inst_bbox);
+  release(d.s_hi);
+  release(d.S64);
+  release(d.s_inst);
+  release(d.axis_s);
+  release(d.axis64);
+  release(d.partial);
+  release(d.amp);
+  release(d.loss_part);
+  release(d.gS);
+  release(d.status);
+  release(d.adj_blocks);
+  release(d.adj_table);
+  release(d.adj_partial);
+  if (p->ev_begin) cudaEventDestroy(p->ev_begin);
+  if (p->ev_end) cudaEventDestroy(p->ev_end);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete p;
+}
+
+extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_options* op,
+                                       scatter_plan_t* out) {
+  if (!out) return fail(SCATTER_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  scatter_status st = validate(pr, op);
+  if (st != SCATTER_OK) return st;
+  int dev = 0, ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(SCATTER_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+
+  std::unique_ptr<scatter_plan_s, void (*)(scatter_plan_t)> p(new scatter_plan_s(), scatter_plan_destroy);
+  p->device = dev;
+  cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  p->s_kind = (scatter_s_kind)pr->s_kind;
+  p->n_atoms = pr->n_atoms;
+  p->n_species = pr->n_species;
+  p->batch = pr->batch;
+  p->lattice_a = pr->lattice_a;
+  p->wavelength = pr->wavelength;
+  p->alpha_i = pr->alpha_i;
+  p->delta = pr->delta;
+  p->beta = pr->beta;
+  p->use_graph = !(op && op->use_graph < 0);
+  if (op && op->timing) {
+    p->timing = true;
+    if ((e = cudaEventCreate(&p->ev_begin)) != cudaSuccess) return cuda_status(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&p->ev_end)) != cudaSuccess) return cuda_status(e, "cudaEventCreate");
+  }
+  scatter_path path = op ? (scatter_path)op->path : SCATTER_PATH_AUTO;
+  if (path == SCATTER_PATH_AUTO) path = SCATTER_PATH_GENERIC;
+  if (path == SCATTER_PATH_SEPARABLE)
+    return fail(SCATTER_ERR_UNSUPPORTED, "separable path is not available for this problem");
+  if (pr->s_kind == SCATTER_S_GID_GRID)
+    return fail(SCATTER_ERR_UNSUPPORTED, "grazing-incidence grids are not available in this build");
+  if (pr->batch > 1 && path != SCATTER_PATH_FP64_REF && path != SCATTER_PATH_GENERIC)
+    return fail(SCATTER_ERR_UNSUPPORTED, "batches run on the generic path");
+  p->path = path;
+
+  // ---- S description --------------------------------------------------------
+  if (pr->s_kind == SCATTER_S_LIST) {
+    p->n_s = pr->n_s;
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      p->n_axis[d] = pr->n_axis[d];
+      p->axis_host[d].assign(pr->axis[d], pr->axis[d] + pr->n_axis[d]);
+    }
+    p->n_s = pr->n_axis[0] * pr->n_axis[1] * pr->n_axis[2];
+  }
+
+  // ---- instances -----------------------------------------------------------------
+  const int B = pr->batch;
+  p->inst.resize(B);
+  for (int b = 0; b < B; ++b) {
+    Instance& in = p->inst[b];
+    in.atom_begin = B > 1 ? pr->atom_off[b] : 0;
+    in.atom_end = B > 1 ? pr->atom_off[b + 1] : pr->n_atoms;
+    in.s_begin = B > 1 ? pr->s_off[b] : 0;
+    in.s_end = B > 1 ? pr->s_off[b + 1] : p->n_s;
+    choose_H(pr, in.s_begin, in.s_end, in.H);
+  }
+
+  // ---- species-sorted, padded slots --------------------------------------------
+  std::vector<int32_t> slot_src, slot_inst;
+  std::vector<int64_t> inst_slot_begin(B);
+  for (int b = 0; b < B; ++b) {
+    Instance& in = p->inst[b];
+    in.slot_begin = (int64_t)slot_src.size();
+    inst_slot_begin[b] = in.slot_begin;
+    std::vector<std::vector<int32_t>> by(pr->n_species);
+    for (int64_t j = in.atom_begin; j < in.atom_end; ++j)
+      by[pr->atom_species ? pr->atom_species[j] : 0].push_back((int32_t)j);
+    for (int s = 0; s < pr->n_species; ++s) {
+      if (by[s].empty()) continue;
+      Segment sg;
+      sg.begin = (int64_t)slot_src.size();
+      for (int32_t j : by[s]) slot_src.push_back(j);
+      while (slot_src.size() % kSlotAlign) slot_src.push_back(-1);
+      sg.end = (int64_t)slot_src.size();
+      sg.species = s;
+      sg.instance = b;
+      p->all_segs.push_back(sg);
+    }
+    in.slot_end = (int64_t)slot_src.size();
+    slot_inst.resize(slot_src.size(), b);
+  }
+  p->n_slots = (int64_t)slot_src.size();
+
+  // ---- device tables --------------------------------------------------------------
+  int64_t bytes = 0;
+  DeviceBuffers& d = p->d;
+  std::vector<float> coef32(kNCoef * pr->n_species);
+  std::vector<double> coef64(kNCoef * pr->n_species);
+  for (int s = 0; s < pr->n_species; ++s) {
+    const scatter_species& sp = pr->species[s];
+    const double v[kNCoef] = {sp.a[0], sp.a[1], sp.a[2], sp.a[3], sp.b[0], sp.b[1],
+                              sp.b[2], sp.b[3], sp.c,    sp.fp,   sp.fpp,  sp.b_dw};
+    for (int i = 0; i < kNCoef; ++i) {
+      coef64[kNCoef * s + i] = v[i];
+      coef32[kNCoef * s + i] = (float)v[i];
+    }
+  }
+  p->coef_host = coef64;
+  std::vector<int64_t> atom_off(B + 1);
+  std::vector<double> inst_H(3 * B);
+  for (int b = 0; b < B; ++b) {
+    atom_off[b] = p->inst[b].atom_begin;
+    for (int dd = 0; dd < 3; ++dd) inst_H[3 * b + dd] = p->inst[b].H[dd];
+  }
+  atom_off[B] = pr->n_atoms;
+  std::vector<int32_t> species_caller(pr->n_atoms, 0);
+  if (pr->atom_species) std::copy(pr->atom_species, pr->atom_species + pr->n_atoms, species_caller.begin());
+
+  if ((st = upload(&d.slot_src, slot_src.data(), slot_src.size(), &bytes))) return st;
+  if ((st = upload(&d.slot_inst, slot_inst.data(), slot_inst.size(), &bytes))) return st;
+  if ((st = upload<float4>(&d.atom4, nullptr, slot_src.size(), &bytes))) return st;
+  if ((st = upload<float>(&d.atom_w, nullptr, slot_src.size(), &bytes))) return st;
+  if ((st = upload(&d.atom_species, species_caller.data(), species_caller.size(), &bytes))) return st;
+  if ((st = upload(&d.coef, coef32.data(), coef32.size(), &bytes))) return st;
+  if ((st = upload(&d.coef64, coef64.data(), coef64.size(), &bytes))) return st;
+  if ((st = upload(&d.atom_off, atom_off.data(), atom_off.size(), &bytes))) return st;
+  if ((st = upload(&d.inst_slot_begin, inst_slot_begin.data(), inst_slot_begin.size(), &bytes))) return st;
+  if ((st = upload(&d.inst_H, inst_H.data(), inst_H.size(), &bytes))) return st;
+  if ((st = upload<double>(&d.inst_shift, nullptr, 3 * (size_t)B, &bytes))) return st;
+  if ((st = upload<unsigned long long>(&d.inst_bbox, nullptr, 6 * (size_t)B, &bytes))) return st;
+  if ((st = upload<unsigned>(&d.status, nullptr, 1, &bytes))) return st;
+  if ((e = cudaMemset(d.inst_shift, 0, 3 * sizeof(double) * B)) != cudaSuccess) return cuda_status(e, "memset");
+  if ((e = cudaMemset(d.status, 0, sizeof(unsigned))) != cudaSuccess) return cuda_status(e, "memset");
+  if (p->n_slots > 0) {
+    if ((e = cudaMemset(d.atom4, 0, sizeof(float4) * p->n_slots)) != cudaSuccess) return cuda_status(e, "memset");
+    if ((e = cudaMemset(d.atom_w, 0, sizeof(float) * p->n_slots)) != cudaSuccess) return cuda_status(e, "memset");
+  }
+
+  if (pr->s_kind == SCATTER_S_LIST) {
+    const int64_t M = p->n_s;
+    std::vector<float> s_hi(3 * (size_t)M);
+    for (int b = 0; b < B; ++b) {
+      const Instance& in = p->inst[b];
+      for (int64_t m = in.s_begin; m < in.s_end; ++m)
+        for (int dd = 0; dd < 3; ++dd) s_hi[(size_t)dd * M + m] = (float)(pr->s_list[3 * m + dd] - in.H[dd]);
+    }
+    for (int64_t m = 0; m < M; ++m)
+      for (int dd = 0; dd < 3; ++dd) p->s_max[dd] = std::max(p->s_max[dd], (double)std::fabs(s_hi[(size_t)dd * M + m]));
+    if ((st = upload(&d.s_hi, s_hi.data(), s_hi.size(), &bytes))) return st;
+    if ((st = upload(&d.S64, pr->s_list, 3 * (size_t)M, &bytes))) return st;
+    if (B > 1) {
+      std::vector<int32_t> s_inst(M);
+      for (int b = 0; b < B; ++b)
+        for (int64_t m = p->inst[b].s_begin; m < p->inst[b].s_end; ++m) s_inst[m] = b;
+      if ((st = upload(&d.s_inst, s_inst.data(), s_inst.size(), &bytes))) return st;
+    }
+  } else {
+    std::vector<float> ax;
+    std::vector<double> ax64;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int64_t i = 0; i < pr->n_axis[dd]; ++i) {
+        ax64.push_back(pr->axis[dd][i]);
+        ax.push_back((float)(pr->axis[dd][i] - p->inst[0].H[dd]));
+        p->s_max[dd] = std::max(p->s_max[dd], std::fabs(pr->axis[dd][i] - p->inst[0].H[dd]));
+      }
+    if ((st = upload(&d.axis_s, ax.data(), ax.size(), &bytes))) return st;
+    if ((st = upload(&d.axis64, ax64.data(), ax64.size(), &bytes))) return st;
+  }
+  // backward workspace (g(S) and per-block loss partials)
+  if (p->n_s > 0) {
+    if ((st = upload<float2>(&d.amp, nullptr, (size_t)p->n_s, &bytes))) return st;
+    if ((st = upload<float2>(&d.gS, nullptr, (size_t)p->n_s, &bytes))) return st;
+  }
+  if ((st = upload<double>(&d.loss_part, nullptr, kLossParts, &bytes))) return st;
+  p->base_bytes = bytes;
+
+  // ---- tiling ------------------------------------------------------------------------
+  if (path == SCATTER_PATH_GENERIC) {
+    Tiling t = heuristic_tiling(p.get());
+    if (op && op->threads) t.threads = op->threads;
+    if (op && op->points_per_thread) t.R = op->points_per_thread;
+    if (op && op->split_k) t.split_k = op->split_k;
+    if (!generic_tiling_supported(t))
+      return fail(SCATTER_ERR_INVALID_ARG, "unsupported tile override (threads=%d R=%d)", t.threads, t.R);
+    if ((st = apply_tiling(p.get(), t))) return st;
+    if (op && op->autotune && !(op->threads || op->points_per_thread || op->split_k)) {
+      if ((st = autotune_generic(p.get(), op->tune_cache))) return st;
+    }
+  } else {
+    Tiling t;
+    t.split_k = 1;
+    if ((st = apply_tiling(p.get(), t))) return st;
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e, "plan synchronize");
+  if (log_enabled())
+    fprintf(stderr, "[scatter] plan: path=%d N=%lld slots=%lld M=%lld threads=%d R=%d split_k=%d\n", (int)p->path,
+            (long long)p->n_atoms, (long long)p->n_slots, (long long)p->n_s, p->tiling.threads, p->tiling.R,
+            p->tiling.split_k);
+  *out = p.release();
+  return SCATTER_OK;
+}

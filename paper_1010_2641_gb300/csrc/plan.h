@@ -1,0 +1,132 @@
+// Internal plan object of libscatter (not part of the public ABI).
+//
+// Device data layout (all owned by the plan, reused by every call):
+//   atoms  : species-sorted, per-instance "slots", each segment of one
+//            (instance, species) padded to a multiple of kSlotAlign with
+//            zero-weight slots so every tile is full and 16-byte aligned.
+//            slot_src[slot]  caller's atom index (or -1 for padding)
+//            atom4[slot]     (x', y', z', c) fp32: x' = r - t (lattice units,
+//                            t the per-call integer centring of the instance),
+//                            c = frac(H . delta) with delta = r - t - rint(r - t)
+//            atom_w[slot]    occupancy (0 for padding)
+//   S      : LIST  -> s_hi[3][M] fp32 (s = S - H), S64[M][3] fp64 (epilogue)
+//            GRID  -> axis_s[d][n_d] fp32, axis64[d][n_d] fp64
+//   chunks : split-K partition of each instance's slots into contiguous
+//            pieces; a chunk is a list of segments (slot range, species).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+#include "scatter_internal.h"
+
+namespace scatter {
+
+constexpr int kSlotAlign = 32;     // padding granularity of species segments
+constexpr int kNCoef = 12;         // a0..a3 b0..b3 c f' f'' B_dw
+constexpr int kMaxSpecies = 64;
+constexpr int kLossParts = 1024;   // per-block partial sums of the misfit
+
+// Status bits written by kernels into plan->d_status.
+enum : unsigned {
+  kStatusNonFinite = 1u,
+  kStatusTimeout = 2u,
+};
+
+struct Segment {
+  int64_t begin;    // first slot
+  int64_t end;      // one past last slot (multiple of kSlotAlign - begin aligned)
+  int32_t species;
+  int32_t instance;
+};
+
+struct Instance {
+  int64_t atom_begin, atom_end;  // caller's atom indices
+  int64_t slot_begin, slot_end;  // device slots
+  int64_t s_begin, s_end;        // output points
+  double H[3];                   // reference reflection (integers)
+};
+
+// Atom block of the adjoint kernel (slots of one species segment).
+struct AdjBlock {
+  int64_t begin;
+  int32_t count;
+  int32_t species;
+};
+
+// Launch shape of the generic kernel.
+struct Tiling {
+  int threads = 256;
+  int R = 8;          // S points per thread
+  int split_k = 1;    // atom chunks per S tile
+};
+
+struct DeviceBuffers {
+  int32_t* slot_src = nullptr;      // [n_slots]
+  int32_t* slot_inst = nullptr;     // [n_slots]
+  float4* atom4 = nullptr;          // [n_slots]
+  float* atom_w = nullptr;          // [n_slots]
+  int32_t* atom_species = nullptr;  // [n_atoms] caller order (FP64 kernel)
+  Segment* segs = nullptr;          // [n_segs] (chunked)
+  int32_t* chunk_seg_off = nullptr; // [n_chunks+1]
+  float* coef = nullptr;            // [n_species][12] fp32
+  double* coef64 = nullptr;         // [n_species][12] fp64
+  int64_t* atom_off = nullptr;      // [batch+1] caller atom ranges
+  int64_t* inst_slot_begin = nullptr; // [batch]
+  double* inst_H = nullptr;         // [batch][3]
+  double* inst_shift = nullptr;     // [batch][3] integer centring t (per call)
+  unsigned long long* inst_bbox = nullptr;  // [batch][6] ordered-int min/max
+  // S
+  float* s_hi = nullptr;            // LIST: [3][M]
+  double* S64 = nullptr;            // LIST: [M][3]
+  int32_t* s_inst = nullptr;        // LIST batch: instance of each point (or null)
+  float* axis_s = nullptr;          // GRID: concatenated axes (s = axis - H)
+  double* axis64 = nullptr;         // GRID: concatenated axes (full S)
+  // workspace
+  float2* partial = nullptr;        // [split_k][M] split-K partials
+  float2* amp = nullptr;            // [M] amplitude scratch (intensity, backward)
+  double* loss_part = nullptr;      // per-block loss partials
+  float2* gS = nullptr;             // [M] adjoint weights g(S)
+  unsigned* status = nullptr;       // [1]
+  // adjoint workspace (allocated on first backward)
+  AdjBlock* adj_blocks = nullptr;
+  float4* adj_table = nullptr;      // [n_species][M][2]
+  float* adj_partial = nullptr;     // [split][n_slots][3]
+};
+
+}  // namespace scatter
+
+struct scatter_plan_s {
+  int device = 0;
+  int n_sm = 0;
+  scatter_path path = SCATTER_PATH_GENERIC;
+  scatter_s_kind s_kind = SCATTER_S_LIST;
+  int64_t n_atoms = 0;
+  int64_t n_slots = 0;
+  int64_t n_s = 0;
+  int32_t n_species = 1;
+  int32_t batch = 1;
+  double lattice_a = 1.0;
+  int64_t n_axis[3] = {0, 0, 0};
+  std::vector<double> axis_host[3];
+  std::vector<double> coef_host;                 // [n_species][12]
+  std::vector<scatter::Instance> inst;
+  std::vector<scatter::Segment> all_segs;        // (instance, species) segments
+  std::vector<scatter::Segment> segs;            // chunk-major
+  std::vector<int32_t> chunk_seg_off;            // [n_chunks+1]
+  std::vector<int64_t> chunk_slots;              // slots per chunk (cost)
+  scatter::Tiling tiling;
+  double wavelength = 0, alpha_i = 0, delta = 0, beta = 0;
+  scatter::DeviceBuffers d;
+  int64_t base_bytes = 0;                        // tables and backward workspace
+  int64_t tiling_bytes = 0;                      // chunk tables and split-K partials
+  double s_max[3] = {0, 0, 0};                   // max |S - H| per axis (error model)
+  bool use_graph = true;
+  bool timing = false;
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+  bool timed_call = false;
+  int32_t last_launches = 0;
+  bool adj_ready = false;
+  int adj_split = 1;
+  int adj_blocks = 0;
+  int64_t adj_s_per_chunk = 0;
+};
