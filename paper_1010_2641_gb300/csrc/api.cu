@@ -56,10 +56,13 @@ scatter_status forward(scatter_plan_t p, const double* xyz, const float* occ, fl
                        cudaStream_t st) {
   p->last_launches = 0;
   if (p->n_s == 0) return SCATTER_OK;
-  if (p->path == SCATTER_PATH_FP64_REF) return launch_f64(p, xyz, occ, amp, inten, st);
+  const bool gid = p->s_kind == SCATTER_S_GID_GRID;
+  if (p->path == SCATTER_PATH_FP64_REF)
+    return gid ? launch_f64_gid(p, xyz, occ, amp, inten, st) : launch_f64(p, xyz, occ, amp, inten, st);
+  if (p->batch > 1) return launch_batch(p, xyz, occ, amp, inten, st);
   scatter_status s = launch_prep(p, xyz, occ, st);
   if (s != SCATTER_OK) return s;
-  return launch_generic(p, amp, inten, st);
+  return gid ? launch_dwba(p, amp, inten, st) : launch_generic(p, amp, inten, st);
 }
 
 }  // namespace

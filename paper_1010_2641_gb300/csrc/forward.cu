@@ -20,13 +20,11 @@
 #include <cstdint>
 #include <cstdio>
 #include "device_common.cuh"
+#include "generic_impl.cuh"
 #include "launch.h"
 
 namespace scatter {
 
-constexpr int kTile = 256;  // atoms per shared-memory stage
-
-enum { kModeList = 0, kModeGrid = 1 };
 
 struct GenericArgs {
   const float4* atom4;
@@ -213,114 +211,17 @@ __global__ void __launch_bounds__(THREADS) k_generic(const GenericArgs a) {
     }
   }
 
-  // ---- atom tiles of this chunk ----------------------------------------------
-  const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
   if (tid == 0) {
     dev::mbar_init(&sh_bar[0], 1);
     dev::mbar_init(&sh_bar[1], 1);
     dev::mbar_fence_init();
   }
   __syncthreads();
-
-  // loader state (used by thread 0 only)
-  int l_seg = seg_lo;
-  int64_t l_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin : 0;
-  auto issue = [&](int stage) {
-    if (l_seg >= seg_hi) return;
-    const int64_t end = a.segs[l_seg].end;
-    const int cnt = (int)dev::min64(kTile, end - l_begin);
-    dev::mbar_arrive_expect_tx(&sh_bar[stage], (uint32_t)cnt * 20u);
-    dev::bulk_g2s(&sh_atom[stage][0], a.atom4 + l_begin, (uint32_t)cnt * 16u, &sh_bar[stage]);
-    dev::bulk_g2s(&sh_w[stage][0], a.atom_w + l_begin, (uint32_t)cnt * 4u, &sh_bar[stage]);
-    l_begin += cnt;
-    if (l_begin >= end && ++l_seg < seg_hi) l_begin = a.segs[l_seg].begin;
-  };
-  if (tid == 0) {
-    issue(0);
-    issue(1);
-  }
-
-  float2 tot[R], sacc[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) tot[r] = sacc[r] = make_float2(0.f, 0.f);
-
-  int c_seg = seg_lo;
-  int64_t c_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin : 0;
+  float2 tot[R];
   int k = 0;
-  bool aborted = false;
-  while (c_seg < seg_hi) {
-    const int64_t end = a.segs[c_seg].end;
-    const int cnt = (int)dev::min64(kTile, end - c_begin);
-    const int st = k & 1;
-    const bool ok = dev::mbar_wait_bounded(&sh_bar[st], (uint32_t)((k >> 1) & 1));
-    float2 acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
-    if (ok) {
-      const float4* at4 = sh_atom[st];
-      const float* atw = sh_w[st];
-#pragma unroll 2
-      for (int j = 0; j < cnt; ++j) {
-        const float4 at = at4[j];
-        const float w = atw[j];
-        if (MODE == kModeGrid) {
-          const float base = fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float f = dev::frac_rn(fmaf(sz[r], at.z, base));
-            float sn, cs;
-            dev::sincos_cycles_mufu(f, &sn, &cs);
-            acc[r].x = fmaf(w, cs, acc[r].x);
-            acc[r].y = fmaf(w, sn, acc[r].y);
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float f = dev::frac_rn(fmaf(sz[r], at.z, fmaf(sy[r], at.y, fmaf(sx[r], at.x, at.w))));
-            float sn, cs;
-            dev::sincos_cycles_mufu(f, &sn, &cs);
-            acc[r].x = fmaf(w, cs, acc[r].x);
-            acc[r].y = fmaf(w, sn, acc[r].y);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      sacc[r].x += acc[r].x;
-      sacc[r].y += acc[r].y;
-    }
-    c_begin += cnt;
-    if (c_begin >= end) {
-      // end of a species segment: fold f_s(|S|)
-      const float* cf = a.coef + kNCoef * a.segs[c_seg].species;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float Sx = a.H[0] + sx[r], Sy = a.H[1] + sy[r], Sz = a.H[2] + sz[r];
-        const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
-        const float2 F = dev::form_factor(cf, s2);
-        const float2 v = dev::cmul(F, sacc[r]);
-        tot[r].x += v.x;
-        tot[r].y += v.y;
-        sacc[r] = make_float2(0.f, 0.f);
-      }
-      if (++c_seg < seg_hi) c_begin = a.segs[c_seg].begin;
-    }
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
-      break;
-    }
-    if (tid == 0) issue(st);
-    ++k;
-  }
-  if (aborted) {
-    if (tid == 0) {
-      dev::set_status(a.status, kStatusTimeout);
-      // drain the copies this CTA still has in flight (bounded)
-      for (int kk = k; kk < k + 2; ++kk) dev::mbar_wait_bounded(&sh_bar[kk & 1], (uint32_t)((kk >> 1) & 1), 1LL << 28);
-    }
+  if (!chunk_sum<MODE, R>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk], a.chunk_seg_off[chunk + 1], a.coef,
+                          a.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status))
     return;
-  }
 
   // ---- epilogue -----------------------------------------------------------------
   if (a.partial) {

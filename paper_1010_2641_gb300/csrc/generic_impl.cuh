@@ -1,0 +1,126 @@
+// The generic kernel's inner pipeline, shared by the one-shot kernel
+// (forward.cu) and the persistent batched kernel (batch.cu).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace scatter {
+
+constexpr int kTile = 256;  // atoms per shared-memory stage
+
+enum { kModeList = 0, kModeGrid = 1 };
+
+// Sum over the atoms of one chunk (a list of species segments) for the R
+// S points of this thread: atom tiles are staged in shared memory by the TMA
+// engine (two stages, mbarrier completion, bounded waits), the per-pair work
+// is the split phase + MUFU sincos + 2 FFMA into tile-blocked FP32 sums, and
+// f_s(|S|) is folded in at the end of every species segment.  `k` counts the
+// tiles this CTA has consumed so far (it sets the stage and mbarrier parity
+// and carries over between chunks of a persistent CTA).  Returns false if a
+// wait gave up (the CTA then drains its copies and must stop).
+template <int MODE, int R>
+__device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, const float* __restrict__ atom_w,
+                                          const Segment* __restrict__ segs, int seg_lo, int seg_hi,
+                                          const float* __restrict__ coef, const float H[3], float inv4a2,
+                                          const float (&sx)[R], const float (&sy)[R], const float (&sz)[R],
+                                          float4 (*sh_atom)[kTile], float (*sh_w)[kTile], uint64_t* sh_bar, int& k,
+                                          float2 (&tot)[R], unsigned* status) {
+  const int tid = threadIdx.x;
+  // loader state (used by thread 0 only)
+  int l_seg = seg_lo;
+  int64_t l_begin = seg_lo < seg_hi ? segs[seg_lo].begin : 0;
+  auto issue = [&](int stage) {
+    if (l_seg >= seg_hi) return;
+    const int64_t end = segs[l_seg].end;
+    const int cnt = (int)dev::min64(kTile, end - l_begin);
+    dev::mbar_arrive_expect_tx(&sh_bar[stage], (uint32_t)cnt * 20u);
+    dev::bulk_g2s(&sh_atom[stage][0], atom4 + l_begin, (uint32_t)cnt * 16u, &sh_bar[stage]);
+    dev::bulk_g2s(&sh_w[stage][0], atom_w + l_begin, (uint32_t)cnt * 4u, &sh_bar[stage]);
+    l_begin += cnt;
+    if (l_begin >= end && ++l_seg < seg_hi) l_begin = segs[l_seg].begin;
+  };
+  if (tid == 0) {
+    issue(k & 1);
+    issue((k + 1) & 1);
+  }
+
+  float2 sacc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) tot[r] = sacc[r] = make_float2(0.f, 0.f);
+
+  int c_seg = seg_lo;
+  int64_t c_begin = seg_lo < seg_hi ? segs[seg_lo].begin : 0;
+  while (c_seg < seg_hi) {
+    const int64_t end = segs[c_seg].end;
+    const int cnt = (int)dev::min64(kTile, end - c_begin);
+    const int st = k & 1;
+    const bool ok = dev::mbar_wait_bounded(&sh_bar[st], (uint32_t)((k >> 1) & 1));
+    float2 acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
+    if (ok) {
+      const float4* at4 = sh_atom[st];
+      const float* atw = sh_w[st];
+#pragma unroll 2
+      for (int j = 0; j < cnt; ++j) {
+        const float4 at = at4[j];
+        const float w = atw[j];
+        if (MODE == kModeGrid) {
+          const float base = fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float f = dev::frac_rn(fmaf(sz[r], at.z, base));
+            float sn, cs;
+            dev::sincos_cycles_mufu(f, &sn, &cs);
+            acc[r].x = fmaf(w, cs, acc[r].x);
+            acc[r].y = fmaf(w, sn, acc[r].y);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float f = dev::frac_rn(fmaf(sz[r], at.z, fmaf(sy[r], at.y, fmaf(sx[r], at.x, at.w))));
+            float sn, cs;
+            dev::sincos_cycles_mufu(f, &sn, &cs);
+            acc[r].x = fmaf(w, cs, acc[r].x);
+            acc[r].y = fmaf(w, sn, acc[r].y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      sacc[r].x += acc[r].x;
+      sacc[r].y += acc[r].y;
+    }
+    c_begin += cnt;
+    if (c_begin >= end) {
+      // end of a species segment: fold f_s(|S|)
+      const float* cf = coef + kNCoef * segs[c_seg].species;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float Sx = H[0] + sx[r], Sy = H[1] + sy[r], Sz = H[2] + sz[r];
+        const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * inv4a2;
+        const float2 F = dev::form_factor(cf, s2);
+        const float2 v = dev::cmul(F, sacc[r]);
+        tot[r].x += v.x;
+        tot[r].y += v.y;
+        sacc[r] = make_float2(0.f, 0.f);
+      }
+      if (++c_seg < seg_hi) c_begin = segs[c_seg].begin;
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        dev::set_status(status, kStatusTimeout);
+        // drain the copies this CTA still has in flight (bounded)
+        for (int kk = k; kk < k + 2; ++kk)
+          dev::mbar_wait_bounded(&sh_bar[kk & 1], (uint32_t)((kk >> 1) & 1), 1LL << 28);
+      }
+      return false;
+    }
+    if (tid == 0) issue(st);
+    ++k;
+  }
+  return true;
+}
+
+}  // namespace scatter

@@ -24,6 +24,20 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
                                const float* I_obs, const float2* G, double* loss_out, float* grad,
                                cudaStream_t st);
 
+// Grazing-incidence (DWBA) path: plan tables, split choice, launches.
+scatter_status prepare_gid(scatter_plan_s* p);
+int dwba_best_split(const scatter_plan_s* p);
+scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
+scatter_status launch_f64_gid(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
+                              float* int_out, cudaStream_t st);
+
+// Batched persistent path (batch > 1): work list, launches (graph-captured).
+scatter_status prepare_batch(scatter_plan_s* p);
+scatter_status launch_batch(scatter_plan_t p, const double* xyz, const float* occ, float2* amp, float* inten,
+                            cudaStream_t st);
+scatter_status enqueue_batch_kernels(scatter_plan_t p, float2* amp, float* inten, cudaStream_t st);
+int batch_blocks_per_sm(int R, int threads);
+
 // Opt-in event timing around the main kernel of a call.
 inline void timing_begin(scatter_plan_s* p, cudaStream_t st) {
   if (p->timing) cudaEventRecord(p->ev_begin, st);

@@ -96,6 +96,8 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
     for (int d = 0; d < 3; ++d)
       if (!is_integer(pr->center_hkl[d]))
         return fail(SCATTER_ERR_INVALID_ARG, "center_hkl must hold integers");
+  if (pr->center_mode == 1 && pr->s_kind == SCATTER_S_GID_GRID && pr->center_hkl[2] != 0.0)
+    return fail(SCATTER_ERR_INVALID_ARG, "grazing-incidence maps use H_z = 0");
   if (pr->batch < 1) return fail(SCATTER_ERR_INVALID_ARG, "batch < 1");
   if (pr->batch > 1) {
     if (pr->s_kind != SCATTER_S_LIST) return fail(SCATTER_ERR_INVALID_ARG, "batches need SCATTER_S_LIST");
@@ -129,7 +131,7 @@ void choose_H(const scatter_problem* pr, int64_t s_begin, int64_t s_end, double 
     if (pr->s_kind == SCATTER_S_LIST) {
       for (int64_t m = s_begin; m < s_end; ++m) sum += pr->s_list[3 * m + d];
       n = s_end - s_begin;
-    } else if (pr->s_kind == SCATTER_S_GRID || d < 2) {
+    } else if (pr->s_kind == SCATTER_S_GRID || d < 2) {  // GID: H_z = 0
       for (int64_t i = 0; i < pr->n_axis[d]; ++i) sum += pr->axis[d][i];
       n = pr->n_axis[d];
     }
@@ -222,6 +224,18 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.loss_part);
   release(d.gS);
   release(d.status);
+  release(d.gid_sz);
+  release(d.gid_sz64);
+  release(d.gid_w);
+  release(d.gid_w64);
+  release(d.ztab);
+  release(d.batch_inst);
+  release(d.batch_items);
+  release(d.counter);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
+  if (p->graph_in) cudaEventDestroy(p->graph_in);
+  if (p->graph_out) cudaEventDestroy(p->graph_out);
   release(d.adj_blocks);
   release(d.adj_table);
   release(d.adj_partial);
@@ -267,8 +281,6 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   if (path == SCATTER_PATH_AUTO) path = SCATTER_PATH_GENERIC;
   if (path == SCATTER_PATH_SEPARABLE)
     return fail(SCATTER_ERR_UNSUPPORTED, "separable path is not available for this problem");
-  if (pr->s_kind == SCATTER_S_GID_GRID)
-    return fail(SCATTER_ERR_UNSUPPORTED, "grazing-incidence grids are not available in this build");
   if (pr->batch > 1 && path != SCATTER_PATH_FP64_REF && path != SCATTER_PATH_GENERIC)
     return fail(SCATTER_ERR_UNSUPPORTED, "batches run on the generic path");
   p->path = path;
@@ -392,7 +404,8 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
       for (int64_t i = 0; i < pr->n_axis[dd]; ++i) {
         ax64.push_back(pr->axis[dd][i]);
         ax.push_back((float)(pr->axis[dd][i] - p->inst[0].H[dd]));
-        p->s_max[dd] = std::max(p->s_max[dd], std::fabs(pr->axis[dd][i] - p->inst[0].H[dd]));
+        if (pr->s_kind == SCATTER_S_GRID || dd < 2)
+          p->s_max[dd] = std::max(p->s_max[dd], std::fabs(pr->axis[dd][i] - p->inst[0].H[dd]));
       }
     if ((st = upload(&d.axis_s, ax.data(), ax.size(), &bytes))) return st;
     if ((st = upload(&d.axis64, ax64.data(), ax64.size(), &bytes))) return st;
@@ -404,9 +417,16 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   }
   if ((st = upload<double>(&d.loss_part, nullptr, kLossParts, &bytes))) return st;
   p->base_bytes = bytes;
+  if (pr->s_kind == SCATTER_S_GID_GRID && (st = prepare_gid(p.get()))) return st;
 
   // ---- tiling ------------------------------------------------------------------------
-  if (path == SCATTER_PATH_GENERIC) {
+  if (path == SCATTER_PATH_GENERIC && pr->s_kind == SCATTER_S_GID_GRID) {
+    Tiling t;
+    t.threads = 256;
+    t.R = 4;
+    t.split_k = op && op->split_k ? op->split_k : dwba_best_split(p.get());
+    if ((st = apply_tiling(p.get(), t))) return st;
+  } else if (path == SCATTER_PATH_GENERIC) {
     Tiling t = heuristic_tiling(p.get());
     if (op && op->threads) t.threads = op->threads;
     if (op && op->points_per_thread) t.R = op->points_per_thread;
@@ -414,7 +434,12 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
     if (!generic_tiling_supported(t))
       return fail(SCATTER_ERR_INVALID_ARG, "unsupported tile override (threads=%d R=%d)", t.threads, t.R);
     if ((st = apply_tiling(p.get(), t))) return st;
-    if (op && op->autotune && !(op->threads || op->points_per_thread || op->split_k)) {
+    if (pr->batch > 1) {
+      if ((st = prepare_batch(p.get()))) return st;
+      if (op && op->autotune && !(op->threads || op->points_per_thread) &&
+          (st = autotune_batch(p.get(), op->tune_cache)))
+        return st;
+    } else if (op && op->autotune && !(op->threads || op->points_per_thread || op->split_k)) {
       if ((st = autotune_generic(p.get(), op->tune_cache))) return st;
     }
   } else {

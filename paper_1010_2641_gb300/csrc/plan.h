@@ -53,6 +53,22 @@ struct AdjBlock {
   int32_t species;
 };
 
+// Instance and work item of the persistent batched kernel.
+struct BatchInst {
+  int64_t s_begin, s_end;
+  int64_t part_off;  // float2 offset of this instance's partials (split > 1)
+  int32_t split;
+  int32_t chunk0;
+  float H[3];
+  float pad;
+};
+
+struct BatchItem {
+  int64_t p0;        // first S point of the tile
+  int32_t inst;
+  int32_t chunk;     // chunk index within the instance
+};
+
 // Launch shape of the generic kernel.
 struct Tiling {
   int threads = 256;
@@ -87,6 +103,16 @@ struct DeviceBuffers {
   double* loss_part = nullptr;      // per-block loss partials
   float2* gS = nullptr;             // [M] adjoint weights g(S)
   unsigned* status = nullptr;       // [1]
+  // grazing incidence (GID grids)
+  float* gid_sz = nullptr;          // [2][n_af] Sz1, Sz2 r.l.u.
+  double* gid_sz64 = nullptr;       // [2][n_af]
+  float2* gid_w = nullptr;          // [4][n_af] beam weights
+  double2* gid_w64 = nullptr;       // [4][n_af]
+  float4* ztab = nullptr;           // [n_afb][n_slots][32] Z1, Z2 per call
+  // batches
+  BatchInst* batch_inst = nullptr;
+  BatchItem* batch_items = nullptr;
+  int* counter = nullptr;
   // adjoint workspace (allocated on first backward)
   AdjBlock* adj_blocks = nullptr;
   float4* adj_table = nullptr;      // [n_species][M][2]
@@ -125,6 +151,15 @@ struct scatter_plan_s {
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   bool timed_call = false;
   int32_t last_launches = 0;
+  // batches: work list and captured graph
+  int32_t batch_items = 0;
+  int batch_ctas = 0;
+  bool batch_has_split = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t graph_in = nullptr, graph_out = nullptr;
+  int32_t graph_launches = 0;
   bool adj_ready = false;
   int adj_split = 1;
   int adj_blocks = 0;

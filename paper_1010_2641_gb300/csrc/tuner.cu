@@ -179,4 +179,51 @@ scatter_status autotune_generic(scatter_plan_s* p, const char* cache_path) {
   return apply_tiling(p, best);
 }
 
+scatter_status autotune_batch(scatter_plan_s* p, const char* cache_path) {
+  if (p->n_s == 0 || p->n_slots == 0) return SCATTER_OK;
+  std::string key = cache_key(p);
+  key.replace(0, 7, "batch");
+  char extra[64];
+  snprintf(extra, sizeof(extra), "|B%d", p->batch);
+  key += extra;
+  Tiling t;
+  if (cache_lookup(cache_path, key, &t) && batch_blocks_per_sm(t.R, t.threads) > 0) {
+    p->tiling = t;
+    return prepare_batch(p);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_ms = 1e30;
+  Tiling best = p->tiling;
+  for (int th : {128, 256})
+    for (int r : {4, 8, 16}) {
+      Tiling c;
+      c.threads = th;
+      c.R = r;
+      c.split_k = 1;
+      p->tiling = c;
+      if (prepare_batch(p) != SCATTER_OK) continue;
+      enqueue_batch_kernels(p, p->d.amp, nullptr, nullptr);  // warm-up
+      cudaEventRecord(e0, nullptr);
+      enqueue_batch_kernels(p, p->d.amp, nullptr, nullptr);
+      cudaEventRecord(e1, nullptr);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (log_enabled()) fprintf(stderr, "[scatter] autotune batch threads=%d R=%d: %.3f ms\n", th, r, ms);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e, "autotune batch");
+  cache_store(cache_path, key, best, best_ms);
+  p->tiling = best;
+  return prepare_batch(p);
+}
+
 }  // namespace scatter

@@ -9,5 +9,7 @@ namespace scatter {
 Tiling heuristic_tiling(const scatter_plan_s* p);
 scatter_status apply_tiling(scatter_plan_s* p, const Tiling& t);
 scatter_status autotune_generic(scatter_plan_s* p, const char* cache_path);
+// Batched plans: (threads, points per thread) of the persistent kernel.
+scatter_status autotune_batch(scatter_plan_s* p, const char* cache_path);
 
 }  // namespace scatter
