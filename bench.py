@@ -44,16 +44,20 @@ MUFU_SINCOS_PER_SM_CLK = 16.0   # measured (scatter_microbench kind 0): 15.97
 MUFU_OPS_PER_PAIR = 2.0         # one sin + one cos per (atom, reflection)
 
 
+GRID = (256, 256, 64)
+
+
 def workload():
     from paper_1010_2641_gb300 import workloads as W
     c = W.fcc_sphere()
-    axes = [W.linspace_axis(0.0, 256, step=0.002), W.linspace_axis(0.0, 256, step=0.002),
-            W.linspace_axis(4.0, 64, step=0.002)]
+    axes = [W.linspace_axis(0.0, GRID[0], step=0.002), W.linspace_axis(0.0, GRID[1], step=0.002),
+            W.linspace_axis(4.0, GRID[2], step=0.002)]
     return c, axes
 
 
-WORKLOAD_NAME = ("strained fcc sphere r=20 cells (134009 atoms, 2 species) x 256x256x64 S grid "
-                 "around (004), step 0.002 r.l.u.")
+def workload_name():
+    return (f"strained fcc sphere r=20 cells (134009 atoms, 2 species) x {GRID[0]}x{GRID[1]}x{GRID[2]} "
+            "S grid around (004), step 0.002 r.l.u.")
 
 
 def sample_indices(n_s: int, n: int, seed: int = 7):
@@ -154,7 +158,7 @@ def run_reference(args, rank, world):
     from paper_1010_2641_gb300 import workloads as W
     oracle.build()
     c, axes = workload()
-    n_s = 256 * 256 * 64
+    n_s = GRID[0] * GRID[1] * GRID[2]
     n_sample = args.ref_sample
     idx = sample_indices(n_s, n_sample, seed=1)
     S = W.grid_points(axes)[idx]
@@ -171,7 +175,7 @@ def run_reference(args, rank, world):
     out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "n_atoms": len(c.xyz), "n_s": n_s,
+           "data": "synthetic", "config": {"workload": workload_name(), "n_atoms": len(c.xyz), "n_s": n_s,
                                            "sample_points": n_sample},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{n_sample} of {n_s} grid points (seeded), all {len(c.xyz)} atoms"},
@@ -194,7 +198,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     c, axes = workload()
-    n_atoms, n_s = len(c.xyz), 256 * 256 * 64
+    n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
     pairs = n_atoms * n_s
     cache = str(ROOT / "gpurun_out" / "tune_cache.jsonl") if args.autotune else None
     plan = api.Plan(c.coef, 5.43, n_atoms, axes=axes, atom_species=c.species, timing=True,
@@ -284,7 +288,7 @@ def run_gpu(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "n_atoms": n_atoms, "n_s": n_s, "pairs_per_step": pairs,
+           "config": {"workload": workload_name(), "n_atoms": n_atoms, "n_s": n_s, "pairs_per_step": pairs,
                       "path": "generic", "threads": info["threads"], "points_per_thread": info["points_per_thread"],
                       "split_k": info["split_k"], "l2": "flushed between steps (256 MB write, outside the events)",
                       "parallelism": f"weak x{world} (independent instance per GPU)"},
@@ -367,7 +371,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--paths", action="store_true")
+    ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
     args = ap.parse_args()
+    if args.grid:
+        global GRID
+        GRID = tuple(int(v) for v in args.grid.split(","))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
