@@ -302,6 +302,43 @@ const char* scatter_status_string(scatter_status status);
 const char* scatter_last_error(void);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free entry point                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * scatter_amplitude_noalloc — for callers that cannot allocate device memory.
+ * The paper has no counterpart: it exists because plans allocate, and some
+ * callers must not — code running while a stream is captured into a CUDA
+ * graph, processes whose device memory belongs to another runtime or pool,
+ * latency-critical loops that may not enter the allocator.  It calls no
+ * cudaMalloc/cudaFree and no allocating library routine.
+ *
+ * Computes T(S) = sum_j w_j exp(+2 i pi S . r_j) for a list of S points with
+ * the generic FP32/MUFU kernel (f == 1: the per-species sum that a caller
+ * multiplies by f_s(|S|) itself).  Positions are used as given (no integer
+ * centring), so keep the crystal near the origin for best precision.
+ *
+ *  n_atoms     0 .. 524,288            n_s  0 .. 1,048,576
+ *  xyz         device float64 [n_atoms][3] (lattice units)
+ *  occ         device float32 [n_atoms] or NULL (all 1)
+ *  S           device float64 [n_s][3] (r.l.u.)
+ *  center_hkl  host double[3], integer reference reflection H near the S
+ *              points (S = H + s with |s| small gives the accurate split)
+ *  T_out       device complex64 [n_s], written in full
+ *  stream      cudaStream_t or NULL
+ *
+ * Scratch: one file-scope __device__ array of 32 MiB per GPU (held from
+ * the library's loading until process exit), shared by every call; calls
+ * that overlap on the GPU race on it and must be serialised by the caller.
+ * The first call on a device looks the array up (cudaGetSymbolAddress)
+ * with that device current: make it before any stream capture.  Sizes
+ * beyond the limits return SCATTER_ERR_INVALID_ARG without launching;
+ * non-finite positions or occupancies contribute nothing.
+ */
+scatter_status scatter_amplitude_noalloc(int64_t n_atoms, const double* xyz, const float* occ, int64_t n_s,
+                                         const double* S, const double* center_hkl, void* T_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Roofline microbenchmarks                                                 */
 /* ------------------------------------------------------------------------ */
 

@@ -100,6 +100,8 @@ _PROTOTYPES = {
     "scatter_status_string": (c_char_p, [c_int32]),
     "scatter_last_error": (c_char_p, []),
     "scatter_microbench": (c_int32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(scatter_microbench_result)]),
+    "scatter_amplitude_noalloc": (c_int32, [c_int64, c_void_p, c_void_p, c_int64, c_void_p,
+                                            ctypes.POINTER(c_double), c_void_p, c_void_p]),
 }
 
 _lib = None

@@ -26,28 +26,6 @@
 namespace scatter {
 
 
-struct GenericArgs {
-  const float4* atom4;
-  const float* atom_w;
-  const Segment* segs;
-  const int32_t* chunk_seg_off;
-  const float* coef;
-  int64_t n_s;
-  const float* s_hi;      // LIST [3][M]
-  const double* S64;      // LIST [M][3]
-  const float* axis_s;    // GRID [n0 | n1 | n2]
-  const double* axis64;   // GRID [n0 | n1 | n2]
-  int64_t n0, n1, n2;
-  float H[3];
-  double H64[3];
-  float inv4a2;
-  const double* shift;    // [3] device, written by prep
-  float2* out_amp;
-  float* out_int;
-  float2* partial;        // split-K partials [chunk][M] (or null)
-  unsigned* status;
-};
-
 // ---------------------------------------------------------------------------
 // prep
 // ---------------------------------------------------------------------------
@@ -412,6 +390,36 @@ scatter_status launch_generic(scatter_plan_t p, float2* amp_out, float* int_out,
     const int64_t nb = (p->n_s + 255) / 256;
     k_reduce<<<(unsigned)nb, 256, 0, st>>>(a, n_chunks, mode_of(p) == kModeGrid);
     p->last_launches += 1;
+  }
+  return cuda_status(cudaGetLastError(), "generic launch");
+}
+
+// Launches the LIST-mode generic kernel (and the split-K reduction) on fully
+// prepared arguments; used by callers that own their buffers.
+scatter_status launch_generic_args(GenericArgs a, int R, int threads, int n_chunks, cudaStream_t st) {
+  void* fn = pick_generic(kModeList, R, threads);
+  if (!fn) return fail(SCATTER_ERR_UNSUPPORTED, "no generic kernel for R=%d threads=%d", R, threads);
+  float2* out_amp = a.out_amp;
+  float* out_int = a.out_int;
+  float2* partial = a.partial;
+  if (n_chunks > 1) {
+    a.out_amp = nullptr;
+    a.out_int = nullptr;
+  } else {
+    a.partial = nullptr;
+  }
+  const int64_t per = (int64_t)threads * R;
+  const int64_t tiles = (a.n_s + per - 1) / per;
+  if (tiles > 0 && n_chunks > 0) {
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)tiles, (unsigned)n_chunks), dim3(threads), args, 0, st);
+    if (e != cudaSuccess) return cuda_status(e, "generic kernel launch");
+  }
+  if (n_chunks > 1 && a.n_s > 0) {
+    a.partial = partial;
+    a.out_amp = out_amp;
+    a.out_int = out_int;
+    k_reduce<<<(unsigned)((a.n_s + 255) / 256), 256, 0, st>>>(a, n_chunks, 0);
   }
   return cuda_status(cudaGetLastError(), "generic launch");
 }

@@ -10,6 +10,31 @@ constexpr int kTile = 256;  // atoms per shared-memory stage
 
 enum { kModeList = 0, kModeGrid = 1 };
 
+struct GenericArgs {
+  const float4* atom4;
+  const float* atom_w;
+  const Segment* segs;
+  const int32_t* chunk_seg_off;
+  const float* coef;
+  int64_t n_s;
+  const float* s_hi;      // LIST [3][M]
+  const double* S64;      // LIST [M][3]
+  const float* axis_s;    // GRID [n0 | n1 | n2]
+  const double* axis64;   // GRID [n0 | n1 | n2]
+  int64_t n0, n1, n2;
+  float H[3];
+  double H64[3];
+  float inv4a2;
+  const double* shift;    // [3] device, written by prep
+  float2* out_amp;
+  float* out_int;
+  float2* partial;        // split-K partials [chunk][M] (or null)
+  unsigned* status;
+};
+
+// LIST-mode generic kernel (+ split-K reduction) on prepared arguments.
+scatter_status launch_generic_args(GenericArgs a, int R, int threads, int n_chunks, cudaStream_t st);
+
 // Sum over the atoms of one chunk (a list of species segments) for the R
 // S points of this thread: atom tiles are staged in shared memory by the TMA
 // engine (two stages, mbarrier completion, bounded waits), the per-pair work
