@@ -121,6 +121,15 @@ class ClockSampler:
 # profile summary -> traffic of the dominant kernel (null if stale)
 # ---------------------------------------------------------------------------
 
+def measured_peak(key: str, fallback: float):
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        v = float(json.loads(p.read_text())[key])
+        return v, f"MEASURED_PEAKS.json {key} = {v} (of measured)"
+    except Exception:
+        return fallback, f"fallback {fallback} (of fallback)"
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha1()
     for f in ("forward.cu", "device_common.cuh", "plan.h"):
@@ -201,8 +210,8 @@ def run_gpu(args, rank, world, local_rank):
     n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
     pairs = n_atoms * n_s
     cache = str(ROOT / "gpurun_out" / "tune_cache.jsonl") if args.autotune else None
-    plan = api.Plan(c.coef, 5.43, n_atoms, axes=axes, atom_species=c.species, timing=True,
-                    autotune=args.autotune, tune_cache=cache)
+    plan = api.Plan(c.coef, 5.43, n_atoms, axes=axes, atom_species=c.species, timing=True, path=args.path,
+                    autotune=args.autotune and args.path == "generic", tune_cache=cache)
     info = plan.info()
     xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
     A = torch.empty(n_s, dtype=torch.complex64, device=dev)
@@ -277,7 +286,19 @@ def run_gpu(args, rank, world, local_rank):
     sm_mhz = clk["sm_mhz"] if clk else None
     n_sm = info["n_sm"]
     roof = None
-    if sm_mhz:
+    if args.path == "separable":
+        # executed tensor-pipe work: 3 split products x 2 flop x M' x N' x K'
+        m_pad = -(-2 * GRID[0] // 128) * 128
+        n_pad = -(-(GRID[1] * GRID[2]) // 256) * 256
+        executed = 6.0 * m_pad * n_pad * 2 * info["n_atoms_padded"]
+        useful = 8.0 * n_atoms * n_s
+        peak, basis = measured_peak("bf16_tflops", 1900.0)
+        achieved = executed / (t_kern * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)",
+                "kernel_ms": t_kern, "useful_tflops": useful / (t_kern * 1e-3) / 1e12,
+                "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+    elif sm_mhz:
         peak = n_sm * MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR * sm_mhz * 1e6 / 1e9  # Gpair/s
         achieved = pairs / (t_kern * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
@@ -287,9 +308,10 @@ def run_gpu(args, rank, world, local_rank):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32" if args.path == "generic" else "f16x3 split, f32 accumulate",
+           "data": "synthetic",
            "config": {"workload": workload_name(), "n_atoms": n_atoms, "n_s": n_s, "pairs_per_step": pairs,
-                      "path": "generic", "threads": info["threads"], "points_per_thread": info["points_per_thread"],
+                      "path": args.path, "threads": info["threads"], "points_per_thread": info["points_per_thread"],
                       "split_k": info["split_k"], "l2": "flushed between steps (256 MB write, outside the events)",
                       "parallelism": f"weak x{world} (independent instance per GPU)"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
@@ -372,6 +394,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--paths", action="store_true")
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
+    ap.add_argument("--path", default="generic", choices=["generic", "separable"])
     args = ap.parse_args()
     if args.grid:
         global GRID

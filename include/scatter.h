@@ -350,7 +350,7 @@ scatter_status scatter_amplitude_noalloc(int64_t n_atoms, const double* xyz, con
  *   0 sin.approx+cos.approx (MUFU ops)   1 ex2.approx (MUFU ops)
  *   2 fma.rn.f32 (lane-ops)              3 fma.rn.f32x2 (lane-ops)
  *   4 fma.rn.f64                         5 generic pair mix (2 MUFU + 7 FFMA)
- *   6 cvt.rni.f32.f32
+ *   6 cvt.rni.f32.f32                    7 cvt.rn.f16x2.f32 (pack ops)
  * It allocates and frees a few KB of device memory and synchronises.
  */
 typedef struct scatter_microbench_result {

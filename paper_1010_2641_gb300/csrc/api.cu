@@ -62,6 +62,7 @@ scatter_status forward(scatter_plan_t p, const double* xyz, const float* occ, fl
   if (p->batch > 1) return launch_batch(p, xyz, occ, amp, inten, st);
   scatter_status s = launch_prep(p, xyz, occ, st);
   if (s != SCATTER_OK) return s;
+  if (p->path == SCATTER_PATH_SEPARABLE) return launch_separable(p, amp, inten, st);
   return gid ? launch_dwba(p, amp, inten, st) : launch_generic(p, amp, inten, st);
 }
 
@@ -140,6 +141,15 @@ extern "C" scatter_status scatter_error_bound(scatter_plan_t p, double radius, d
     return fail(SCATTER_ERR_INVALID_ARG, "bad argument");
   const double u = std::ldexp(1.0, -24);  // fp32 unit roundoff
   const double pi = 3.14159265358979323846;
+  if (p->path == SCATTER_PATH_SEPARABLE) {
+    // tables in FP32 (sincospif, ~2 ulp) and f16 hi + lo operands (three
+    // products: the dropped lo.lo term is below 2^-22 of each term)
+    const double sr = (p->s_max[0] + p->s_max[1] + p->s_max[2]) * radius;
+    *per_pair = 2.0 * pi * u * (2.0 * sr + 2.0) + 4.0 * std::ldexp(1.0, -22) + 6.0 * u;
+    const double steps = (double)std::max<int64_t>(p->n_slots, 1) / 16.0;
+    *rel_l2_random = *per_pair + u * std::sqrt(4096.0 + steps / 256.0 + (double)p->tiling.split_k);
+    return SCATTER_OK;
+  }
   if (p->path == SCATTER_PATH_FP64_REF) {
     // FP64 phases |S.r| <= |S| (radius + |t|): bounded by the output rounding
     *per_pair = u;

@@ -31,6 +31,10 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
 scatter_status launch_f64_gid(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
                               float* int_out, cudaStream_t st);
 
+// Separable tensor-core path (GRID plans): tables, tiling, launches.
+scatter_status prepare_separable(scatter_plan_s* p, int split_override);
+scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
+
 // Batched persistent path (batch > 1): work list, launches (graph-captured).
 scatter_status prepare_batch(scatter_plan_s* p);
 scatter_status launch_batch(scatter_plan_t p, const double* xyz, const float* occ, float2* amp, float* inten,

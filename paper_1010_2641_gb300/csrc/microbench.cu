@@ -14,6 +14,7 @@
 //   kind 4  fma.rn.f64                    (FP64 FMA ops)
 //   kind 5  2 MUFU + 7 FFMA per "pair"    (pairs: the generic-kernel mix)
 //   kind 6  cvt.rni.f32.f32               (round-to-integer ops)
+//   kind 7  cvt.rn.f16x2.f32              (pack ops: 2 floats -> f16x2)
 //
 // Every kernel runs a fixed number of independent dependency chains per thread
 // so that latency is hidden; results are written out so nothing is eliminated.
@@ -121,6 +122,15 @@ __global__ void ub_kernel(float* out, int iters, long long* cycles) {
         a[i] = fmaf(a[i], m, c0);
         b[i] = fmaf(b[i], m, c0);
       }
+    } else if (KIND == 7) {
+#pragma unroll
+      for (int i = 0; i < kChains; ++i) {
+        uint32_t h;
+        asm volatile("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(a[i]), "f"(b[i]));
+        a[i] = __uint_as_float(h) + 1.0f;
+        asm volatile("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(b[i]), "f"(a[i]));
+        b[i] = __uint_as_float(h) + 1.0f;
+      }
     } else if (KIND == 6) {
 #pragma unroll
       for (int i = 0; i < kChains; ++i) {
@@ -151,6 +161,7 @@ double ops_per_iter(int kind) {
     case 4: return 2.0 * kChains;   // DFMA
     case 5: return 1.0 * kChains;   // generic pairs
     case 6: return 2.0 * kChains;   // FRND
+    case 7: return 2.0 * kChains;   // F2F pack
   }
   return 0.0;
 }
@@ -159,7 +170,7 @@ double ops_per_iter(int kind) {
 
 extern "C" scatter_status scatter_microbench(int kind, int iters,
                                              scatter_microbench_result* res) {
-  if (!res || kind < 0 || kind > 6 || iters <= 0) return SCATTER_ERR_INVALID_ARG;
+  if (!res || kind < 0 || kind > 7 || iters <= 0) return SCATTER_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCATTER_ERR_NO_DEVICE;
   cudaDeviceProp prop;
@@ -186,6 +197,7 @@ extern "C" scatter_status scatter_microbench(int kind, int iters,
       case 4: ub_kernel<4><<<blocks, threads>>>(out, n_iter, cyc); break;
       case 5: ub_kernel<5><<<blocks, threads>>>(out, n_iter, cyc); break;
       case 6: ub_kernel<6><<<blocks, threads>>>(out, n_iter, cyc); break;
+      case 7: ub_kernel<7><<<blocks, threads>>>(out, n_iter, cyc); break;
     }
   };
   launch(16);  // warm-up

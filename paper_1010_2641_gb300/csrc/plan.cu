@@ -229,6 +229,10 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.gid_w);
   release(d.gid_w64);
   release(d.ztab);
+  release(d.sep_A);
+  release(d.sep_Y);
+  release(d.sep_Z);
+  release(d.sep_partial);
   release(d.batch_inst);
   release(d.batch_items);
   release(d.counter);
@@ -279,8 +283,8 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   }
   scatter_path path = op ? (scatter_path)op->path : SCATTER_PATH_AUTO;
   if (path == SCATTER_PATH_AUTO) path = SCATTER_PATH_GENERIC;
-  if (path == SCATTER_PATH_SEPARABLE)
-    return fail(SCATTER_ERR_UNSUPPORTED, "separable path is not available for this problem");
+  if (path == SCATTER_PATH_SEPARABLE && (pr->s_kind != SCATTER_S_GRID || pr->batch != 1))
+    return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid (SCATTER_S_GRID)");
   if (pr->batch > 1 && path != SCATTER_PATH_FP64_REF && path != SCATTER_PATH_GENERIC)
     return fail(SCATTER_ERR_UNSUPPORTED, "batches run on the generic path");
   p->path = path;
@@ -420,7 +424,9 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   if (pr->s_kind == SCATTER_S_GID_GRID && (st = prepare_gid(p.get()))) return st;
 
   // ---- tiling ------------------------------------------------------------------------
-  if (path == SCATTER_PATH_GENERIC && pr->s_kind == SCATTER_S_GID_GRID) {
+  if (path == SCATTER_PATH_SEPARABLE) {
+    if ((st = prepare_separable(p.get(), op ? op->split_k : 0))) return st;
+  } else if (path == SCATTER_PATH_GENERIC && pr->s_kind == SCATTER_S_GID_GRID) {
     Tiling t;
     t.threads = 256;
     t.R = 4;

@@ -109,6 +109,11 @@ struct DeviceBuffers {
   float2* gid_w = nullptr;          // [4][n_af] beam weights
   double2* gid_w64 = nullptr;       // [4][n_af]
   float4* ztab = nullptr;           // [n_afb][n_slots][32] Z1, Z2 per call
+  // separable path
+  void* sep_A = nullptr;            // A operand blocks (f16 hi/lo)
+  float2* sep_Y = nullptr;          // [n1][n_slots]
+  float2* sep_Z = nullptr;          // [n_slots][n2]
+  float* sep_partial = nullptr;     // [split][2][n_s] planar
   // batches
   BatchInst* batch_inst = nullptr;
   BatchItem* batch_items = nullptr;
@@ -160,6 +165,7 @@ struct scatter_plan_s {
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;
   int32_t graph_launches = 0;
+  int64_t sep_mt = 0, sep_nt = 0, sep_steps = 0;
   bool adj_ready = false;
   int adj_split = 1;
   int adj_blocks = 0;

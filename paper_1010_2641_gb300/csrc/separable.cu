@@ -1,0 +1,544 @@
+// Separable tensor-core path for axis-aligned S grids (tcgen05, sm_103a).
+//
+// On a grid S = H + (s_a, s_b, s_c) the phase of Eq. 2 separates,
+//   exp(2 i pi (c_j + s_a x'_j + s_b y'_j + s_c z'_j)) = X[a,j] Y[b,j] Zw[c,j] / w_j
+// with X = e^{2 pi i s_a x'}, Y = e^{2 pi i s_b y'}, Zw = w e^{2 pi i (c + s_c z')},
+// so the per-species sum is a complex matrix product over the atoms:
+//   T_s[a, (b,c)] = sum_{j in s} X[a,j] B[(b,c), j],   B = Y[b,j] Zw[c,j].
+// It runs as a real GEMM D = A B^T on the 5th-generation tensor cores:
+//   A  (M = 2 n_a rows: Re/Im of each a) x (K = 2 per atom: Re/Im):
+//      rows 2a: [Xr, -Xi], rows 2a+1: [Xi, Xr]  -> D[2a] = Re T, D[2a+1] = Im T
+//   B  (N = (b,c) points) x (K): [Br, Bi]
+// Both operands are split into f16 hi + lo parts and three products
+// (hi.hi + hi.lo + lo.hi) accumulate in FP32 in tensor memory (TMEM), which
+// keeps the result near FP32 accuracy (the lo.lo term is below 2^-22).
+//
+// Per call: k_sep_tables writes the A operand (hi/lo, already in the
+// canonical no-swizzle K-major shared-memory layout, one 16 KB block per
+// (M tile, 16-atom step)) and the Y, Zw tables.  k_sep: CTA = one 128-row
+// M tile x one 256-point N tile x one atom chunk; per 16-atom step the TMA
+// engine copies the A block, all threads form the B block (complex products,
+// f16 split) in shared memory, and one thread issues 6 tcgen05.mma
+// (2 K16 sub-steps x 3 products, M=128 N=256).  A four-stage ring for the
+// A blocks (the TMA runs two steps ahead), a two-stage ring for the B blocks
+// and register prefetch of the next step's Y, Zw values keep the formation
+// of step k+1 overlapped with the MMAs of step k.
+// Every 256 steps and at every species boundary the accumulator is read
+// from TMEM (tcgen05.ld), multiplied by f_s(|S|) and added into planar FP32
+// partials owned by the CTA; k_sep_reduce sums the chunks in order and
+// applies the translation phase.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <vector>
+#include "device_common.cuh"
+#include "launch.h"
+#include "tuner.h"
+
+namespace scatter {
+
+constexpr int kSepThreads = 256;
+constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
+constexpr int kSepN = 256;                 // MMA N (points per CTA)
+constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
+constexpr int kSepFlush = 256;             // steps between TMEM flushes
+constexpr uint32_t kSepABytes = 16384;     // A block: hi + lo, 128 x 32 f16 each
+constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
+constexpr int kSepAStages = 4;             // A ring: TMA runs two steps ahead
+constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
+constexpr size_t kSepSmem = kSepAStages * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + alignment slack
+constexpr uint32_t kSepTmemCols = 256;
+
+// -------------------------------------------------------------------------
+// descriptors (PTX tcgen05 shared-memory and instruction descriptors)
+// -------------------------------------------------------------------------
+
+// No-swizzle K-major operand: 8-row x 16-byte core matrices; lbo = byte
+// stride between core matrices along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor core
+  return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// kind::f16: D f32, A and B f16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kSepIdesc = (1u << 4) | ((uint32_t)(kSepN >> 3) << 17) | ((uint32_t)(kSepM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kSepIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   dev::smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// f16 hi/lo split of two floats packed as f16x2 each.
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(y), "f"(x));
+  const __half2 h = *reinterpret_cast<const __half2*>(&hi);
+  const float2 hf = __half22float2(h);
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - hf.y), "f"(x - hf.x));
+}
+
+// -------------------------------------------------------------------------
+// tables
+// -------------------------------------------------------------------------
+
+struct SepTabArgs {
+  const float4* atom4;
+  const float* atom_w;
+  const float* axis_s;  // [n0 | n1 | n2] s values
+  int64_t n0, n1, n2;
+  int64_t n_slots, n_steps, n_mt;
+  uint4* A;             // [n_mt][n_steps][hi|lo][4 kb][16 mg][8 rows] of 16 B
+  float2* Y;            // [n1][n_slots]
+  float2* Zw;           // [n_slots][n2]
+};
+
+// One thread per 16-byte row of a core matrix of the A operand (4 atoms x
+// Re/Im of one row m), hi and lo parts.
+__global__ void k_sep_tab_a(const SepTabArgs t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = t.n_mt * t.n_steps * 4 * kSepM;
+  if (i >= total) return;
+  const int r = (int)(i % 8), mg = (int)((i / 8) % 16), kb = (int)((i / 128) % 4);
+  const int64_t ks = (i / 512) % t.n_steps, mt = i / (512 * t.n_steps);
+  const int64_t m = mt * kSepM + mg * 8 + r;
+  const int64_t a = m >> 1;
+  const int ri = (int)(m & 1);
+  float v[8];
+  const float sa = a < t.n0 ? t.axis_s[a] : 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t slot = ks * kSepStep + kb * 4 + q;
+    float sn = 0.f, cs = 0.f;
+    if (a < t.n0) {
+      const float p = sa * t.atom4[slot].x;
+      sincospif(2.0f * (p - rintf(p)), &sn, &cs);
+    }
+    // row 2a: (Xr, -Xi); row 2a+1: (Xi, Xr)
+    v[2 * q] = ri ? sn : cs;
+    v[2 * q + 1] = ri ? cs : -sn;
+  }
+  uint4 hi, lo;
+  split2(v[0], v[1], hi.x, lo.x);
+  split2(v[2], v[3], hi.y, lo.y);
+  split2(v[4], v[5], hi.z, lo.z);
+  split2(v[6], v[7], hi.w, lo.w);
+  uint4* blk = t.A + (mt * t.n_steps + ks) * (kSepABytes / 16);
+  const int64_t off = (int64_t)(kb * 16 + mg) * 8 + r;
+  blk[off] = hi;
+  blk[512 + off] = lo;
+}
+
+__global__ void k_sep_tab_yz(const SepTabArgs t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ny = t.n1 * t.n_slots, nz = t.n_slots * t.n2;
+  if (i < ny) {
+    const int64_t b = i / t.n_slots, slot = i % t.n_slots;
+    const float p = t.axis_s[t.n0 + b] * t.atom4[slot].y;
+    float sn, cs;
+    sincospif(2.0f * (p - rintf(p)), &sn, &cs);
+    t.Y[i] = make_float2(cs, sn);
+  } else if (i < ny + nz) {
+    const int64_t k = i - ny, slot = k / t.n2, c = k % t.n2;
+    const float4 at = t.atom4[slot];
+    const float p = fmaf(t.axis_s[t.n0 + t.n1 + c], at.z, at.w);
+    float sn, cs;
+    sincospif(2.0f * (p - rintf(p)), &sn, &cs);
+    const float w = t.atom_w[slot];
+    t.Zw[k] = make_float2(w * cs, w * sn);
+  }
+}
+
+// -------------------------------------------------------------------------
+// main kernel
+// -------------------------------------------------------------------------
+
+struct SepArgs {
+  const uint4* A;
+  const float2* Y;
+  const float2* Zw;
+  const Segment* segs;
+  const int32_t* chunk_seg_off;
+  const float* coef;
+  const float* axis_s;
+  int64_t n0, n1, n2, n_s;
+  int64_t n_slots, n_steps, n_mt, n_nt;
+  float H[3];
+  float inv4a2;
+  float* partial;   // [chunk][2][n_s] planar (re plane, im plane)
+  unsigned* status;
+};
+
+__global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
+  extern __shared__ __align__(1024) unsigned char sep_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[kSepAStages];
+  __shared__ __align__(8) uint64_t bar_mma[kSepBStages];
+  __shared__ uint32_t tmem_slot;
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(sep_smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* ringA = smem;
+  unsigned char* ringB = smem + kSepAStages * kSepABytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t mt = blockIdx.x % a.n_mt, nt = blockIdx.x / a.n_mt;
+  const int chunk = blockIdx.y;
+  const int64_t nbc = a.n1 * a.n2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dev::smem_addr(&tmem_slot)),
+                 "r"(kSepTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kSepAStages; ++s) dev::mbar_init(&bar_full[s], 1);
+    for (int s = 0; s < kSepBStages; ++s) dev::mbar_init(&bar_mma[s], 1);
+    dev::mbar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // this thread's B row: point bc of the N tile
+  const int64_t bc = nt * kSepN + tid;
+  const bool row_ok = bc < nbc;
+  const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
+  const float2* Yrow = a.Y + rb * a.n_slots;
+  const float2* Zcol = a.Zw + rc;
+  const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+
+  const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
+  const uint4* Ablk = a.A + mt * a.n_steps * (kSepABytes / 16);
+  float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
+  float* part_im = part_re + a.n_s;
+  // the chunk's steps are contiguous; species boundaries fall on step edges
+  const int64_t ks_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin / kSepStep : 0;
+  const int64_t ks_end = seg_lo < seg_hi ? a.segs[seg_hi - 1].end / kSepStep : 0;
+
+  auto issue_a = [&](int64_t ks, int64_t g) {
+    const int st = (int)(g & (kSepAStages - 1));
+    dev::mbar_arrive_expect_tx(&bar_full[st], kSepABytes);
+    dev::bulk_g2s(ringA + st * kSepABytes, Ablk + ks * (kSepABytes / 16), kSepABytes, &bar_full[st]);
+  };
+  auto load_yz = [&](int64_t ks, float2 (&y)[kSepStep], float2 (&z)[kSepStep]) {
+    const int64_t slot0 = ks * kSepStep;
+#pragma unroll
+    for (int q = 0; q < kSepStep; ++q) {
+      y[q] = row_ok ? __ldg(Yrow + slot0 + q) : make_float2(0.f, 0.f);
+      z[q] = row_ok ? __ldg(Zcol + (slot0 + q) * a.n2) : make_float2(0.f, 0.f);
+    }
+  };
+  if (tid == 0) {
+    for (int d = 0; d < 2; ++d)
+      if (ks_begin + d < ks_end) issue_a(ks_begin + d, d);
+  }
+  float2 cy[kSepStep], cz[kSepStep];
+  if (ks_begin < ks_end) load_yz(ks_begin, cy, cz);
+
+  int64_t g = 0;  // steps issued by this CTA
+  bool ok = true;
+  bool first_flush = true;
+  int cur_seg = seg_lo;
+  int64_t seg_end_ks = seg_lo < seg_hi ? a.segs[seg_lo].end / kSepStep : 0;
+  int64_t grp_start = ks_begin;
+
+  for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
+    const int bst = (int)(g & (kSepBStages - 1));
+    const int ast = (int)(g & (kSepAStages - 1));
+    unsigned char* sB = ringB + bst * kSepBBytes;
+    // B stage bst and A stage of step g-2 are free once the MMAs of g-2 completed
+    bool w_ok = true;
+    if (g >= 2) w_ok = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)(((g - 2) >> 1) & 1));
+    if (tid == 0 && w_ok && ks + 2 < ks_end) issue_a(ks + 2, g + 2);
+    // prefetch the next step's Y, Zw into registers, then form this step's B
+    float2 ny[kSepStep], nz[kSepStep];
+    if (ks + 1 < ks_end) load_yz(ks + 1, ny, nz);
+    if (w_ok) {
+#pragma unroll
+      for (int kb = 0; kb < 4; ++kb) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 y = cy[kb * 4 + q], z = cz[kb * 4 + q];
+          split2(fmaf(y.x, z.x, -y.y * z.y), fmaf(y.x, z.y, y.y * z.x), hi[q], lo[q]);
+        }
+        *reinterpret_cast<uint4*>(sB + kb * 4096 + b_row_off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (__syncthreads_or(!w_ok)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g >> 2) & 1))) {
+        dev::set_status(a.status, kStatusTimeout);
+      } else {
+        tc_fence_after();
+        const uint32_t aA = dev::smem_addr(ringA + ast * kSepABytes), aB = dev::smem_addr(sB);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint64_t a_hi = smem_desc(aA + u * 4096, 2048, 128);
+          const uint64_t a_lo = smem_desc(aA + 8192 + u * 4096, 2048, 128);
+          const uint64_t b_hi = smem_desc(aB + u * 8192, 4096, 128);
+          const uint64_t b_lo = smem_desc(aB + 16384 + u * 8192, 4096, 128);
+          const uint32_t acc0 = (ks > grp_start || u > 0) ? 1u : 0u;
+          mma_f16(tmem, a_hi, b_hi, acc0);
+          mma_f16(tmem, a_hi, b_lo, 1u);
+          mma_f16(tmem, a_lo, b_hi, 1u);
+        }
+      }
+      mma_commit(&bar_mma[bst]);
+    }
+#pragma unroll
+    for (int q = 0; q < kSepStep; ++q) {
+      cy[q] = ny[q];
+      cz[q] = nz[q];
+    }
+    const bool seg_done = ks + 1 == seg_end_ks;
+    if (!seg_done && ks + 1 - grp_start < kSepFlush) continue;
+
+    // ---- flush: TMEM -> f_s(|S|) x T -> planar partials --------------------
+    const bool d_ok = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)((g >> 1) & 1));
+    if (__syncthreads_or(!d_ok)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    const float* cf = a.coef + kNCoef * a.segs[cur_seg].species;
+    const int sub = warp & 3;
+    const int col0 = (warp >> 2) * 128;
+    const int64_t m_row = mt * kSepM + sub * 32 + lane;  // A row = 2a + ri
+    const int64_t pa = m_row >> 1;
+    const bool is_im = (m_row & 1) != 0;
+    const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
+#pragma unroll 1
+    for (int cc = 0; cc < 128; cc += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(col0 + cc), v);
+      const int64_t bc0 = nt * kSepN + col0 + cc;
+      int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
+      float res[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
+        const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
+        const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
+        const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
+        const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
+        const float2 F = dev::form_factor(cf, s2);
+        res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
+        if (++ic == a.n2) {
+          ic = 0;
+          ++ib;
+        }
+      }
+      if (pa < a.n0 && bc0 < nbc) {
+        float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
+        if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+          float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
+            o.x += res[4 * q];
+            o.y += res[4 * q + 1];
+            o.z += res[4 * q + 2];
+            o.w += res[4 * q + 3];
+            d4[q] = o;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+        }
+      }
+    }
+    first_flush = false;
+    tc_fence_before();
+    __syncthreads();
+    grp_start = ks + 1;
+    if (seg_done && ++cur_seg < seg_hi) seg_end_ks = a.segs[cur_seg].end / kSepStep;
+  }
+  if (ok && first_flush) {
+    // empty chunk: its partials are zero
+    const int sub = warp & 3;
+    const int col0 = (warp >> 2) * 128;
+    const int64_t m_row = mt * kSepM + sub * 32 + lane;
+    const int64_t pa = m_row >> 1;
+    if (pa < a.n0) {
+      float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
+      for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+    }
+  }
+  if (!ok) {
+    dev::set_status(a.status, kStatusTimeout);
+    // wait (bounded) for MMAs still in flight before releasing TMEM
+    if (tid == 0 && g > 0)
+      dev::mbar_wait_bounded(&bar_mma[(g - 1) & (kSepBStages - 1)], (uint32_t)(((g - 1) >> 1) & 1), 1LL << 28);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSepTmemCols));
+}
+
+// Sum of the planar chunk partials in order, translation phase, outputs.
+__global__ void k_sep_reduce(const float* __restrict__ partial, int split, int64_t n_s, const double* __restrict__ axis64,
+                             int64_t n0, int64_t n1, int64_t n2, double H0, double H1, double H2,
+                             const double* __restrict__ shift, float2* out_amp, float* out_int) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_s) return;
+  float2 v = make_float2(0.f, 0.f);
+  for (int c = 0; c < split; ++c) {
+    v.x += partial[(int64_t)c * 2 * n_s + m];
+    v.y += partial[(int64_t)c * 2 * n_s + n_s + m];
+  }
+  if (shift[0] != 0.0 || shift[1] != 0.0 || shift[2] != 0.0) {
+    const int64_t i2 = m % n2, line = m / n2, i1 = line % n1, i0 = line / n1;
+    v = dev::cmul(dev::shift_phase(axis64[i0] - H0, axis64[n0 + i1] - H1, axis64[n0 + n1 + i2] - H2, shift), v);
+  }
+  if (out_amp) out_amp[m] = v;
+  if (out_int) out_int[m] = v.x * v.x + v.y * v.y;
+}
+
+// -------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------
+
+namespace {
+
+int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
+  const double cap = (double)p->n_sm;  // one CTA per SM (TMEM + shared memory)
+  const double steps = (double)std::max<int64_t>(p->n_slots / kSepStep, 1);
+  double best = 1e300;
+  int best_k = 1;
+  for (int k = 1; k <= 64; ++k) {
+    if (k > 1 && steps / k < 64) break;
+    const double cost = std::ceil((double)tiles * k / cap) * (steps / k + 40.0) +
+                        (k > 1 ? 0.01 * k * (double)p->n_s / cap : 0.0);
+    if (cost < best * 0.995) {
+      best = cost;
+      best_k = k;
+    }
+  }
+  return best_k;
+}
+
+}  // namespace
+
+scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
+  if (p->s_kind != SCATTER_S_GRID || p->batch != 1)
+    return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid");
+  if (p->n_slots % kSepStep) return fail(SCATTER_ERR_UNSUPPORTED, "slot padding is not a multiple of 16");
+  const int64_t n_steps = p->n_slots / kSepStep;
+  const int64_t n_mt = (2 * p->n_axis[0] + kSepM - 1) / kSepM;
+  const int64_t n_nt = (p->n_axis[1] * p->n_axis[2] + kSepN - 1) / kSepN;
+  const int split = split_override > 0 ? split_override : sep_best_split(p, n_mt * n_nt);
+  Tiling t;
+  t.threads = 256;
+  t.R = 8;
+  t.split_k = split;
+  // chunk tables (segments) as for the generic path; the partial buffer is planar
+  scatter_status st = apply_tiling(p, t);
+  if (st != SCATTER_OK) return st;
+  p->sep_mt = n_mt;
+  p->sep_nt = n_nt;
+  p->sep_steps = n_steps;
+  cudaError_t e;
+  const size_t a_bytes = (size_t)n_mt * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
+  const size_t y_bytes = (size_t)p->n_axis[1] * (size_t)std::max<int64_t>(p->n_slots, 1) * sizeof(float2);
+  const size_t z_bytes = (size_t)std::max<int64_t>(p->n_slots, 1) * (size_t)p->n_axis[2] * sizeof(float2);
+  const size_t part_bytes = (size_t)split * 2 * (size_t)p->n_s * sizeof(float);
+  if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
+  if ((e = cudaMalloc(&p->d.sep_Y, y_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Y");
+  if ((e = cudaMalloc(&p->d.sep_Z, z_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Z");
+  if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
+    return cuda_status(e, "cudaMalloc separable partials");
+  p->base_bytes += (int64_t)(a_bytes + y_bytes + z_bytes + part_bytes);
+  if ((e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem)) != cudaSuccess)
+    return cuda_status(e, "separable shared memory attribute");
+  return SCATTER_OK;
+}
+
+scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st) {
+  SepTabArgs t{};
+  t.atom4 = p->d.atom4;
+  t.atom_w = p->d.atom_w;
+  t.axis_s = p->d.axis_s;
+  t.n0 = p->n_axis[0];
+  t.n1 = p->n_axis[1];
+  t.n2 = p->n_axis[2];
+  t.n_slots = p->n_slots;
+  t.n_steps = p->sep_steps;
+  t.n_mt = p->sep_mt;
+  t.A = static_cast<uint4*>(p->d.sep_A);
+  t.Y = p->d.sep_Y;
+  t.Zw = p->d.sep_Z;
+  const int n_chunks = (int)p->chunk_seg_off.size() - 1;
+  if (p->n_slots > 0) {
+    const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;
+    k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
+    const int64_t nyz = p->n_axis[1] * p->n_slots + p->n_slots * p->n_axis[2];
+    k_sep_tab_yz<<<(unsigned)((nyz + 255) / 256), 256, 0, st>>>(t);
+    p->last_launches += 2;
+  }
+  SepArgs a{};
+  a.A = static_cast<const uint4*>(p->d.sep_A);
+  a.Y = p->d.sep_Y;
+  a.Zw = p->d.sep_Z;
+  a.segs = p->d.segs;
+  a.chunk_seg_off = p->d.chunk_seg_off;
+  a.coef = p->d.coef;
+  a.axis_s = p->d.axis_s;
+  a.n0 = p->n_axis[0];
+  a.n1 = p->n_axis[1];
+  a.n2 = p->n_axis[2];
+  a.n_s = p->n_s;
+  a.n_slots = p->n_slots;
+  a.n_steps = p->sep_steps;
+  a.n_mt = p->sep_mt;
+  a.n_nt = p->sep_nt;
+  for (int d = 0; d < 3; ++d) a.H[d] = (float)p->inst[0].H[d];
+  a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
+  a.partial = p->d.sep_partial;
+  a.status = p->d.status;
+  dim3 grid((unsigned)(p->sep_mt * p->sep_nt), (unsigned)std::max(n_chunks, 1));
+  timing_begin(p, st);
+  k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
+  timing_end(p, st);
+  p->last_launches += 1;
+  k_sep_reduce<<<(unsigned)((p->n_s + 255) / 256), 256, 0, st>>>(
+      p->d.sep_partial, std::max(n_chunks, 1), p->n_s, p->d.axis64, p->n_axis[0], p->n_axis[1], p->n_axis[2],
+      p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, amp_out, int_out);
+  p->last_launches += 1;
+  return cuda_status(cudaGetLastError(), "separable launch");
+}
+
+}  // namespace scatter
