@@ -15,11 +15,13 @@
 //
 // Per call: k_sep_tables writes the A operand (hi/lo, already in the
 // canonical no-swizzle K-major shared-memory layout, one 16 KB block per
-// (M tile, 16-atom step)) and the Y, Zw tables.  k_sep: CTA = one 128-row
-// M tile x one 256-point N tile x one atom chunk; per 16-atom step the TMA
-// engine copies the A block, all threads form the B block (complex products,
-// f16 split) in shared memory, and one thread issues 6 tcgen05.mma
-// (2 K16 sub-steps x 3 products, M=128 N=256).  A four-stage ring for the
+// (M tile, 16-atom step), the two tiles of a pair adjacent) and the Y, Zw
+// tables.  k_sep: CTA = a pair of 128-row M tiles (two 128 x 256 FP32
+// accumulators filling the 512 TMEM columns) x one 256-point N tile x one
+// atom chunk; per 16-atom step the TMA engine copies the pair's A blocks,
+// all threads form the B block (complex products, f16 split) in shared
+// memory once for both tiles, and one thread issues 12 tcgen05.mma
+// (2 tiles x 2 K16 sub-steps x 3 products, M=128 N=256).  A four-stage ring for the
 // A blocks (the TMA runs two steps ahead), a two-stage ring for the B blocks
 // and register prefetch of the next step's Y, Zw values keep the formation
 // of step k+1 overlapped with the MMAs of step k.
@@ -43,12 +45,13 @@ constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
 constexpr int kSepN = 256;                 // MMA N (points per CTA)
 constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
 constexpr int kSepFlush = 256;             // steps between TMEM flushes
-constexpr uint32_t kSepABytes = 16384;     // A block: hi + lo, 128 x 32 f16 each
+constexpr uint32_t kSepABytes = 16384;     // A block of one M tile: hi + lo, 128 x 32 f16 each
+constexpr int kSepPair = 2;                // M tiles per CTA (one formed B tile feeds both)
 constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
 constexpr int kSepAStages = 4;             // A ring: TMA runs two steps ahead
 constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
-constexpr size_t kSepSmem = kSepAStages * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + alignment slack
-constexpr uint32_t kSepTmemCols = 256;
+constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
+constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
 
 // -------------------------------------------------------------------------
 // descriptors (PTX tcgen05 shared-memory and instruction descriptors)
@@ -116,7 +119,7 @@ struct SepTabArgs {
   const float* axis_s;  // [n0 | n1 | n2] s values
   int64_t n0, n1, n2;
   int64_t n_slots, n_steps, n_mt;
-  uint4* A;             // [n_mt][n_steps][hi|lo][4 kb][16 mg][8 rows] of 16 B
+  uint4* A;             // [n_mt/2][n_steps][2 tiles][hi|lo][4 kb][16 mg][8 rows] of 16 B
   float2* Y;            // [n1][n_slots]
   float2* Zw;           // [n_slots][n2]
 };
@@ -151,7 +154,7 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
   split2(v[2], v[3], hi.y, lo.y);
   split2(v[4], v[5], hi.z, lo.z);
   split2(v[6], v[7], hi.w, lo.w);
-  uint4* blk = t.A + (mt * t.n_steps + ks) * (kSepABytes / 16);
+  uint4* blk = t.A + (((mt >> 1) * t.n_steps + ks) * kSepPair + (mt & 1)) * (kSepABytes / 16);
   const int64_t off = (int64_t)(kb * 16 + mg) * 8 + r;
   blk[off] = hi;
   blk[512 + off] = lo;
@@ -205,9 +208,11 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(sep_smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* ringA = smem;
-  unsigned char* ringB = smem + kSepAStages * kSepABytes;
+  unsigned char* ringB = smem + kSepAStages * kSepPair * kSepABytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t mt = blockIdx.x % a.n_mt, nt = blockIdx.x / a.n_mt;
+  const int64_t n_mp = (a.n_mt + 1) / 2;
+  const int64_t mp = blockIdx.x % n_mp, nt = blockIdx.x / n_mp;
+  const int ntp = 2 * mp + 1 < a.n_mt ? 2 : 1;  // M tiles of this CTA with rows
   const int chunk = blockIdx.y;
   const int64_t nbc = a.n1 * a.n2;
 
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
   const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
 
   const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
-  const uint4* Ablk = a.A + mt * a.n_steps * (kSepABytes / 16);
+  const uint4* Ablk = a.A + mp * a.n_steps * (kSepPair * kSepABytes / 16);
   float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
   float* part_im = part_re + a.n_s;
   // the chunk's steps are contiguous; species boundaries fall on step edges
@@ -244,8 +249,9 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
 
   auto issue_a = [&](int64_t ks, int64_t g) {
     const int st = (int)(g & (kSepAStages - 1));
-    dev::mbar_arrive_expect_tx(&bar_full[st], kSepABytes);
-    dev::bulk_g2s(ringA + st * kSepABytes, Ablk + ks * (kSepABytes / 16), kSepABytes, &bar_full[st]);
+    const uint32_t bytes = (uint32_t)ntp * kSepABytes;
+    dev::mbar_arrive_expect_tx(&bar_full[st], bytes);
+    dev::bulk_g2s(ringA + st * kSepPair * kSepABytes, Ablk + ks * (kSepPair * kSepABytes / 16), bytes, &bar_full[st]);
   };
   auto load_yz = [&](int64_t ks, float2 (&y)[kSepStep], float2 (&z)[kSepStep]) {
     const int64_t slot0 = ks * kSepStep;
@@ -303,17 +309,21 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
         dev::set_status(a.status, kStatusTimeout);
       } else {
         tc_fence_after();
-        const uint32_t aA = dev::smem_addr(ringA + ast * kSepABytes), aB = dev::smem_addr(sB);
+        const uint32_t aB = dev::smem_addr(sB);
+        for (int tp = 0; tp < ntp; ++tp) {
+          const uint32_t aA = dev::smem_addr(ringA + (ast * kSepPair + tp) * kSepABytes);
+          const uint32_t d = tmem + (uint32_t)(tp * kSepN);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const uint64_t a_hi = smem_desc(aA + u * 4096, 2048, 128);
-          const uint64_t a_lo = smem_desc(aA + 8192 + u * 4096, 2048, 128);
-          const uint64_t b_hi = smem_desc(aB + u * 8192, 4096, 128);
-          const uint64_t b_lo = smem_desc(aB + 16384 + u * 8192, 4096, 128);
-          const uint32_t acc0 = (ks > grp_start || u > 0) ? 1u : 0u;
-          mma_f16(tmem, a_hi, b_hi, acc0);
-          mma_f16(tmem, a_hi, b_lo, 1u);
-          mma_f16(tmem, a_lo, b_hi, 1u);
+          for (int u = 0; u < 2; ++u) {
+            const uint64_t a_hi = smem_desc(aA + u * 4096, 2048, 128);
+            const uint64_t a_lo = smem_desc(aA + 8192 + u * 4096, 2048, 128);
+            const uint64_t b_hi = smem_desc(aB + u * 8192, 4096, 128);
+            const uint64_t b_lo = smem_desc(aB + 16384 + u * 8192, 4096, 128);
+            const uint32_t acc0 = (ks > grp_start || u > 0) ? 1u : 0u;
+            mma_f16(d, a_hi, b_hi, acc0);
+            mma_f16(d, a_hi, b_lo, 1u);
+            mma_f16(d, a_lo, b_hi, 1u);
+          }
         }
       }
       mma_commit(&bar_mma[bst]);
@@ -336,48 +346,50 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
     const float* cf = a.coef + kNCoef * a.segs[cur_seg].species;
     const int sub = warp & 3;
     const int col0 = (warp >> 2) * 128;
-    const int64_t m_row = mt * kSepM + sub * 32 + lane;  // A row = 2a + ri
-    const int64_t pa = m_row >> 1;
-    const bool is_im = (m_row & 1) != 0;
-    const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
-#pragma unroll 1
-    for (int cc = 0; cc < 128; cc += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(col0 + cc), v);
-      const int64_t bc0 = nt * kSepN + col0 + cc;
-      int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
-      float res[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
-        const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
-        const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
-        const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
-        const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
-        const float2 F = dev::form_factor(cf, s2);
-        res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
-        if (++ic == a.n2) {
-          ic = 0;
-          ++ib;
-        }
-      }
-      if (pa < a.n0 && bc0 < nbc) {
-        float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
-        if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-          float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
-            o.x += res[4 * q];
-            o.y += res[4 * q + 1];
-            o.z += res[4 * q + 2];
-            o.w += res[4 * q + 3];
-            d4[q] = o;
+    for (int tp = 0; tp < ntp; ++tp) {
+      const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;  // A row = 2a + ri
+      const int64_t pa = m_row >> 1;
+      const bool is_im = (m_row & 1) != 0;
+      const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
+  #pragma unroll 1
+      for (int cc = 0; cc < 128; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
+        const int64_t bc0 = nt * kSepN + col0 + cc;
+        int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
+        float res[32];
+  #pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
+          const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
+          const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
+          const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
+          const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
+          const float2 F = dev::form_factor(cf, s2);
+          res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
+          if (++ic == a.n2) {
+            ic = 0;
+            ++ib;
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+        }
+        if (pa < a.n0 && bc0 < nbc) {
+          float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
+          if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+  #pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
+              o.x += res[4 * q];
+              o.y += res[4 * q + 1];
+              o.z += res[4 * q + 2];
+              o.w += res[4 * q + 3];
+              d4[q] = o;
+            }
+          } else {
+  #pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+          }
         }
       }
     }
@@ -391,11 +403,13 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
     // empty chunk: its partials are zero
     const int sub = warp & 3;
     const int col0 = (warp >> 2) * 128;
-    const int64_t m_row = mt * kSepM + sub * 32 + lane;
-    const int64_t pa = m_row >> 1;
-    if (pa < a.n0) {
-      float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
-      for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+    for (int tp = 0; tp < ntp; ++tp) {
+      const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
+      const int64_t pa = m_row >> 1;
+      if (pa < a.n0) {
+        float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
+        for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+      }
     }
   }
   if (!ok) {
@@ -441,8 +455,10 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
   int best_k = 1;
   for (int k = 1; k <= 64; ++k) {
     if (k > 1 && steps / k < 64) break;
-    const double cost = std::ceil((double)tiles * k / cap) * (steps / k + 40.0) +
-                        (k > 1 ? 0.01 * k * (double)p->n_s / cap : 0.0);
+    // one step ~1 us of MMA; an extra chunk costs one planar partial of the
+    // map (8 B per point written once, read once by the reduction)
+    const double part_steps = 16.0 * (double)p->n_s / 6.0e12 / 1.0e-6;
+    const double cost = std::ceil((double)tiles * k / cap) * (steps / k + 40.0) + (k > 1 ? k * part_steps : 0.0);
     if (cost < best * 0.995) {
       best = cost;
       best_k = k;
@@ -460,7 +476,8 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   const int64_t n_steps = p->n_slots / kSepStep;
   const int64_t n_mt = (2 * p->n_axis[0] + kSepM - 1) / kSepM;
   const int64_t n_nt = (p->n_axis[1] * p->n_axis[2] + kSepN - 1) / kSepN;
-  const int split = split_override > 0 ? split_override : sep_best_split(p, n_mt * n_nt);
+  const int64_t n_mp = (n_mt + 1) / 2;
+  const int split = split_override > 0 ? split_override : sep_best_split(p, n_mp * n_nt);
   Tiling t;
   t.threads = 256;
   t.R = 8;
@@ -472,7 +489,7 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   p->sep_nt = n_nt;
   p->sep_steps = n_steps;
   cudaError_t e;
-  const size_t a_bytes = (size_t)n_mt * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
+  const size_t a_bytes = (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
   const size_t y_bytes = (size_t)p->n_axis[1] * (size_t)std::max<int64_t>(p->n_slots, 1) * sizeof(float2);
   const size_t z_bytes = (size_t)std::max<int64_t>(p->n_slots, 1) * (size_t)p->n_axis[2] * sizeof(float2);
   const size_t part_bytes = (size_t)split * 2 * (size_t)p->n_s * sizeof(float);
@@ -503,7 +520,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   t.Zw = p->d.sep_Z;
   const int n_chunks = (int)p->chunk_seg_off.size() - 1;
   if (p->n_slots > 0) {
-    const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;
+    const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;  // real tiles; a padding tile is never read
     k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
     const int64_t nyz = p->n_axis[1] * p->n_slots + p->n_slots * p->n_axis[2];
     k_sep_tab_yz<<<(unsigned)((nyz + 255) / 256), 256, 0, st>>>(t);
@@ -529,7 +546,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.partial = p->d.sep_partial;
   a.status = p->d.status;
-  dim3 grid((unsigned)(p->sep_mt * p->sep_nt), (unsigned)std::max(n_chunks, 1));
+  dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)std::max(n_chunks, 1));
   timing_begin(p, st);
   k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
   timing_end(p, st);
