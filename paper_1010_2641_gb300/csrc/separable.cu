@@ -40,9 +40,7 @@
 
 namespace scatter {
 
-constexpr int kSepFormThreads = 256;       // one B row per thread; all warps run the epilogue
-constexpr int kSepThreads = kSepFormThreads;
-constexpr int kSepCtl = 0;                 // the thread that issues TMA copies and MMAs
+constexpr int kSepThreads = 256;
 constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
 constexpr int kSepN = 256;                 // MMA N (points per CTA)
 constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
@@ -103,14 +101,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// f16 hi/lo split of two floats packed as f16x2 each: hi keeps the top 11
-// significand bits (exact in f16 over its normal range), lo = x - hi is
-// exact in FP32 and rounded once to f16; no conversion back to FP32.
+// f16 hi/lo split of two floats packed as f16x2 each.
 __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
-  const float xh = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  const float yh = __uint_as_float(__float_as_uint(y) & 0xFFFFE000u);
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(yh), "f"(xh));
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - yh), "f"(x - xh));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(y), "f"(x));
+  const __half2 h = *reinterpret_cast<const __half2*>(&hi);
+  const float2 hf = __half22float2(h);
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - hf.y), "f"(x - hf.x));
 }
 
 // -------------------------------------------------------------------------
@@ -236,9 +232,8 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
   const uint32_t tmem = tmem_slot;
 
   // this thread's B row: point bc of the N tile
-  const bool former = tid < kSepFormThreads;
-  const int64_t bc = nt * kSepN + (former ? tid : 0);
-  const bool row_ok = former && bc < nbc;
+  const int64_t bc = nt * kSepN + tid;
+  const bool row_ok = bc < nbc;
   const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
   const float2* Yrow = a.Y + rb * a.n_slots;
   const float2* Zcol = a.Zw + rc;
@@ -266,14 +261,12 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
       z[q] = row_ok ? __ldg(Zcol + (slot0 + q) * a.n2) : make_float2(0.f, 0.f);
     }
   };
-  if (tid == kSepCtl) {
+  if (tid == 0) {
     for (int d = 0; d < 2; ++d)
       if (ks_begin + d < ks_end) issue_a(ks_begin + d, d);
   }
   float2 cy[kSepStep], cz[kSepStep];
-#pragma unroll
-  for (int q = 0; q < kSepStep; ++q) cy[q] = cz[q] = make_float2(0.f, 0.f);
-  if (former && ks_begin < ks_end) load_yz(ks_begin, cy, cz);
+  if (ks_begin < ks_end) load_yz(ks_begin, cy, cz);
 
   int64_t g = 0;  // steps issued by this CTA
   bool ok = true;
@@ -289,13 +282,11 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
     // B stage bst and A stage of step g-2 are free once the MMAs of g-2 completed
     bool w_ok = true;
     if (g >= 2) w_ok = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)(((g - 2) >> 1) & 1));
-    if (tid == kSepCtl && w_ok && ks + 2 < ks_end) issue_a(ks + 2, g + 2);
+    if (tid == 0 && w_ok && ks + 2 < ks_end) issue_a(ks + 2, g + 2);
     // prefetch the next step's Y, Zw into registers, then form this step's B
     float2 ny[kSepStep], nz[kSepStep];
-#pragma unroll
-    for (int q = 0; q < kSepStep; ++q) ny[q] = nz[q] = make_float2(0.f, 0.f);
-    if (former && ks + 1 < ks_end) load_yz(ks + 1, ny, nz);
-    if (former && w_ok) {
+    if (ks + 1 < ks_end) load_yz(ks + 1, ny, nz);
+    if (w_ok) {
 #pragma unroll
       for (int kb = 0; kb < 4; ++kb) {
         uint32_t hi[4], lo[4];
@@ -313,7 +304,7 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
       ok = false;
       break;
     }
-    if (tid == kSepCtl) {
+    if (tid == 0) {
       if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g >> 2) & 1))) {
         dev::set_status(a.status, kStatusTimeout);
       } else {
@@ -355,7 +346,7 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
     const float* cf = a.coef + kNCoef * a.segs[cur_seg].species;
     const int sub = warp & 3;
     const int col0 = (warp >> 2) * 128;
-    for (int tp = 0; tp < (former ? ntp : 0); ++tp) {
+    for (int tp = 0; tp < ntp; ++tp) {
       const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;  // A row = 2a + ri
       const int64_t pa = m_row >> 1;
       const bool is_im = (m_row & 1) != 0;
@@ -408,7 +399,7 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
     grp_start = ks + 1;
     if (seg_done && ++cur_seg < seg_hi) seg_end_ks = a.segs[cur_seg].end / kSepStep;
   }
-  if (ok && first_flush && former) {
+  if (ok && first_flush) {
     // empty chunk: its partials are zero
     const int sub = warp & 3;
     const int col0 = (warp >> 2) * 128;
@@ -424,7 +415,7 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
   if (!ok) {
     dev::set_status(a.status, kStatusTimeout);
     // wait (bounded) for MMAs still in flight before releasing TMEM
-    if (tid == kSepCtl && g > 0)
+    if (tid == 0 && g > 0)
       dev::mbar_wait_bounded(&bar_mma[(g - 1) & (kSepBStages - 1)], (uint32_t)(((g - 1) >> 1) & 1), 1LL << 28);
   }
   tc_fence_before();
