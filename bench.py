@@ -4,22 +4,27 @@ Workload (one step = one pass of the hot path over the synthetic input):
 strained spherical fcc nanocrystal of 134,009 atoms (radius 20 cells,
 Si-like core / Ge-like shell, radial strain + thermal noise) scattering onto
 a 256 x 256 x 64 grid of S points (step 0.002 r.l.u.) around (004):
-per-call prep (centring, split phase) + the generic FP32/MUFU kernel +
-epilogue, 5.6e11 atom-reflection pairs per step.
+per-call prep (centring, split phase), the map kernel and the epilogue,
+5.6e11 atom-reflection pairs per step.  The headline uses the separable
+tensor-core path (--path separable, the default) or the generic FP32/MUFU
+path (--path generic); both meet the 1e-4 relative-L2 tolerance on this map,
+which the CPU-baseline leg re-checks against the FP64 oracle on a sample.
 
 Metric: atom-reflection pairs per second (whole job, all ranks), the paper's
 "reflections x atoms / s" (Section 2.2).  Each rank runs its own full
 instance (weak scaling, no collective on the data path).
 
 JSON line keys beyond the base contract:
-  roofline      dominant kernel (generic) against the MUFU bound
-                16 sin/cos ops / SM / clk -> 8 pairs / SM / clk x SMs x clock
+  roofline      dominant kernel: k_sep against the measured dense tensor
+                peak, or k_generic against the MUFU bound
+                (16 sin/cos ops / SM / clk -> 8 pairs / SM / clk x SMs x clock)
   cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample
   accuracy      relative L2 error of the GPU map vs the oracle on that sample
   e2e           the same metric through the public API with host buffers
                 (positions H2D from pinned memory, map D2H every step)
-  paths         other rows measured on their own workloads (FP64 kernel,
-                adjoint) when --paths is given
+  paths         the other rows on their own workloads: the other map path
+                (with its roofline), the FP64 kernel, the adjoint, the DWBA
+                map and the batched persistent launch (skip: --no-paths)
 """
 from __future__ import annotations
 
@@ -334,35 +339,53 @@ def run_gpu(args, rank, world, local_rank):
                                "sample": f"{len(idx)} of {n_s} grid points (seeded), all {n_atoms} atoms, {dt:.1f} s"}
         out["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                            "points": int(len(idx)), "tolerance": 1e-4}
-    if args.paths and rank == 0:
-        out["paths"] = measure_paths(args, dev)
+    if not args.no_paths and rank == 0 and world == 1:
+        out["paths"] = measure_paths(args, dev, clk)
     plan.check()
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
 
 
-def measure_paths(args, dev):
-    """Other rows of the hot path on their own workloads (device time)."""
+def _time_calls(fn, plan, reps=2):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        fn()
+        ms.append(plan.timing()[0])
+    return float(np.mean(ms))
+
+
+def measure_paths(args, dev, clk):
+    """The other rows of the hot path, each on its own workload (device time
+    of the row's main kernel, CUDA events on the launching stream)."""
     import torch
     from paper_1010_2641_gb300 import api
     from paper_1010_2641_gb300 import workloads as W
     res = {}
-    # plain FP64 kernel on a 1/64 slice of the sphere map (every 64th l-plane pair)
     c, axes = workload()
+    xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
+    n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
+    # generic FP32/MUFU kernel on the full strained-sphere map, with its roofline
+    other = "generic" if args.path == "separable" else "separable"
+    plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, path=other, timing=True)
+    ms = _time_calls(lambda: plan.amplitude(xyz), plan)
+    row = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "workload": "strained sphere, full map"}
+    if other == "generic" and clk and clk.get("sm_mhz"):
+        peak = plan.info()["n_sm"] * 8.0 * clk["sm_mhz"] * 1e6
+        row["roofline"] = {"bound": "alu", "achieved": n_atoms * n_s / (ms * 1e-3) / 1e9, "peak": peak / 1e9,
+                           "unit": "Gpair/s", "frac": n_atoms * n_s / (ms * 1e-3) / peak}
+    res[f"{other}_sphere"] = row
+    del plan
+    # plain FP64 kernel on a 1/16 slice of the same map (every 16th l plane)
     sub = [axes[0], axes[1], axes[2][::16]]
-    n_s = len(sub[0]) * len(sub[1]) * len(sub[2])
-    for path in ("fp64", "generic"):
-        plan = api.Plan(c.coef, W.LATTICE_A, len(c.xyz), axes=sub, atom_species=c.species, path=path, timing=True)
-        xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
-        plan.amplitude(xyz)
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(2):
-            plan.amplitude(xyz)
-            ms.append(plan.timing()[0])
-        res[f"{path}_sphere_sub"] = {"value": len(c.xyz) * n_s / (np.mean(ms) * 1e-3), "unit": UNIT,
-                                     "n_s": n_s, "kernel_ms": float(np.mean(ms))}
+    n_sub = len(sub[0]) * len(sub[1]) * len(sub[2])
+    plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=sub, atom_species=c.species, path="fp64", timing=True)
+    ms = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
+    res["fp64_sphere_slice"] = {"value": n_atoms * n_sub / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "n_s": n_sub}
+    del plan, xyz
     # adjoint on the strained cube (102,400 atoms x 128^3)
     cube = W.strained_cube()
     ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
@@ -371,14 +394,31 @@ def measure_paths(args, dev):
     x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
     I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
     A = plan.amplitude(x)
-    plan.backward(x, A, I_obs)
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(2):
-        plan.backward(x, A, I_obs)
-        ms.append(plan.timing()[0])
-    res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (np.mean(ms) * 1e-3), "unit": UNIT,
-                           "kernel_ms": float(np.mean(ms))}
+    ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
+    ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
+    res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                           "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr"}
+    del plan, x, A, I_obs
+    # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
+    isl = W.truncated_pyramid()
+    gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
+    plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
+                    gid=gid, timing=True)
+    x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
+    ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+    m_gid = 512 * 512 * 32
+    res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
+                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams"}
+    del plan, x
+    # batched persistent launch, CUDA-graph replay (64 uneven crystals)
+    bx, bs, bcoef, bS, ao, so = W.ewald_batch()
+    plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True)
+    x = torch.tensor(bx, dtype=torch.float64, device=dev)
+    out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
+    ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
+    pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
+    res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
+                          "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each"}
     return res
 
 
@@ -392,9 +432,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--paths", action="store_true")
+    ap.add_argument("--no-paths", action="store_true", help="skip the other rows' measurements")
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
-    ap.add_argument("--path", default="generic", choices=["generic", "separable"])
+    ap.add_argument("--path", default="separable", choices=["generic", "separable"],
+                    help="kernel family of the headline line (both meet the 1e-4 tolerance on this map)")
     args = ap.parse_args()
     if args.grid:
         global GRID
