@@ -408,7 +408,14 @@ def measure_paths(args, dev, clk):
     ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
     m_gid = 512 * 512 * 32
     res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
-                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams"}
+                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel"}
+    del plan
+    plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
+                    gid=gid, path="separable", timing=True)
+    ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+    res["dwba_island_separable"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
+                                    "kernel_ms": ms,
+                                    "workload": "same map, beams stacked on a virtual l axis, tensor cores"}
     del plan, x
     # batched persistent launch, CUDA-graph replay (64 uneven crystals)
     bx, bs, bcoef, bS, ao, so = W.ewald_batch()

@@ -62,7 +62,7 @@ scatter_status forward(scatter_plan_t p, const double* xyz, const float* occ, fl
   if (p->batch > 1) return launch_batch(p, xyz, occ, amp, inten, st);
   scatter_status s = launch_prep(p, xyz, occ, st);
   if (s != SCATTER_OK) return s;
-  if (p->path == SCATTER_PATH_SEPARABLE) return launch_separable(p, amp, inten, st);
+  if (p->path == SCATTER_PATH_SEPARABLE) return launch_separable(p, amp, inten, st);  // GRID and GID_GRID
   return gid ? launch_dwba(p, amp, inten, st) : launch_generic(p, amp, inten, st);
 }
 

@@ -28,6 +28,7 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
 scatter_status prepare_gid(scatter_plan_s* p);
 int dwba_best_split(const scatter_plan_s* p);
 scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
+scatter_status launch_gid_combine(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
 scatter_status launch_f64_gid(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
                               float* int_out, cudaStream_t st);
 

@@ -233,6 +233,9 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.sep_Y);
   release(d.sep_Z);
   release(d.sep_partial);
+  release(d.sep_axis_s);
+  release(d.sep_axis64);
+  release(d.sep_virt);
   release(d.batch_inst);
   release(d.batch_items);
   release(d.counter);
@@ -283,8 +286,8 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   }
   scatter_path path = op ? (scatter_path)op->path : SCATTER_PATH_AUTO;
   if (path == SCATTER_PATH_AUTO) path = SCATTER_PATH_GENERIC;
-  if (path == SCATTER_PATH_SEPARABLE && (pr->s_kind != SCATTER_S_GRID || pr->batch != 1))
-    return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid (SCATTER_S_GRID)");
+  if (path == SCATTER_PATH_SEPARABLE && (pr->s_kind == SCATTER_S_LIST || pr->batch != 1))
+    return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid (GRID or GID_GRID)");
   if (pr->batch > 1 && path != SCATTER_PATH_FP64_REF && path != SCATTER_PATH_GENERIC)
     return fail(SCATTER_ERR_UNSUPPORTED, "batches run on the generic path");
   p->path = path;

@@ -113,7 +113,10 @@ struct DeviceBuffers {
   void* sep_A = nullptr;            // A operand blocks (f16 hi/lo)
   float2* sep_Y = nullptr;          // [n1][n_slots]
   float2* sep_Z = nullptr;          // [n_slots][n2]
-  float* sep_partial = nullptr;     // [split][2][n_s] planar
+  float* sep_partial = nullptr;     // [split][2][sep_ns] planar
+  float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
+  double* sep_axis64 = nullptr;     // separable grid axes, full S
+  float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid
   // batches
   BatchInst* batch_inst = nullptr;
   BatchItem* batch_items = nullptr;
@@ -166,6 +169,9 @@ struct scatter_plan_s {
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;
   int32_t graph_launches = 0;
   int64_t sep_mt = 0, sep_nt = 0, sep_steps = 0;
+  int64_t sep_n[3] = {0, 0, 0};                  // separable grid shape (GID: n_h, n_k, 4 n_af)
+  int64_t sep_ns = 0;
+  std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
   bool adj_ready = false;
   int adj_split = 1;
   int adj_blocks = 0;

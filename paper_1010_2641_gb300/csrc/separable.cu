@@ -457,7 +457,7 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
     if (k > 1 && steps / k < 64) break;
     // one step ~1 us of MMA; an extra chunk costs one planar partial of the
     // map (8 B per point written once, read once by the reduction)
-    const double part_steps = 16.0 * (double)p->n_s / 6.0e12 / 1.0e-6;
+    const double part_steps = 16.0 * (double)p->sep_ns / 6.0e12 / 1.0e-6;
     const double cost = std::ceil((double)tiles * k / cap) * (steps / k + 40.0) + (k > 1 ? k * part_steps : 0.0);
     if (cost < best * 0.995) {
       best = cost;
@@ -469,13 +469,42 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
 
 }  // namespace
 
+// The separable grid: the plan's own axes, or for a grazing-incidence plan
+// the virtual grid (h, k, l) whose l axis stacks the four beams' Sz values
+// [Sz1 | Sz2 | -Sz2 | -Sz1] over alpha_f, so each beam is a plain grid sum.
 scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
-  if (p->s_kind != SCATTER_S_GRID || p->batch != 1)
+  const bool gid = p->s_kind == SCATTER_S_GID_GRID;
+  if ((p->s_kind != SCATTER_S_GRID && !gid) || p->batch != 1)
     return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid");
   if (p->n_slots % kSepStep) return fail(SCATTER_ERR_UNSUPPORTED, "slot padding is not a multiple of 16");
+  std::vector<double> ax64[3];
+  for (int d = 0; d < 2; ++d) ax64[d] = p->axis_host[d];
+  if (gid) {
+    const int64_t n_af = p->n_axis[2];
+    ax64[2].resize(4 * n_af);
+    for (int64_t i = 0; i < n_af; ++i) {
+      const double z1 = p->gid_sz_host[i], z2 = p->gid_sz_host[n_af + i];
+      ax64[2][i] = z1;
+      ax64[2][n_af + i] = z2;
+      ax64[2][2 * n_af + i] = -z2;
+      ax64[2][3 * n_af + i] = -z1;
+    }
+  } else {
+    ax64[2] = p->axis_host[2];
+  }
+  std::vector<double> all64;
+  std::vector<float> alls;
+  for (int d = 0; d < 3; ++d) {
+    p->sep_n[d] = (int64_t)ax64[d].size();
+    for (double v : ax64[d]) {
+      all64.push_back(v);
+      alls.push_back((float)(v - p->inst[0].H[d]));
+    }
+  }
+  p->sep_ns = p->sep_n[0] * p->sep_n[1] * p->sep_n[2];
   const int64_t n_steps = p->n_slots / kSepStep;
-  const int64_t n_mt = (2 * p->n_axis[0] + kSepM - 1) / kSepM;
-  const int64_t n_nt = (p->n_axis[1] * p->n_axis[2] + kSepN - 1) / kSepN;
+  const int64_t n_mt = (2 * p->sep_n[0] + kSepM - 1) / kSepM;
+  const int64_t n_nt = (p->sep_n[1] * p->sep_n[2] + kSepN - 1) / kSepN;
   const int64_t n_mp = (n_mt + 1) / 2;
   const int split = split_override > 0 ? split_override : sep_best_split(p, n_mp * n_nt);
   Tiling t;
@@ -485,20 +514,33 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   // chunk tables (segments) as for the generic path; the partial buffer is planar
   scatter_status st = apply_tiling(p, t);
   if (st != SCATTER_OK) return st;
+  if (p->d.partial) {  // the generic path's partials are not used here
+    cudaFree(p->d.partial);
+    p->d.partial = nullptr;
+  }
   p->sep_mt = n_mt;
   p->sep_nt = n_nt;
   p->sep_steps = n_steps;
   cudaError_t e;
   const size_t a_bytes = (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
-  const size_t y_bytes = (size_t)p->n_axis[1] * (size_t)std::max<int64_t>(p->n_slots, 1) * sizeof(float2);
-  const size_t z_bytes = (size_t)std::max<int64_t>(p->n_slots, 1) * (size_t)p->n_axis[2] * sizeof(float2);
-  const size_t part_bytes = (size_t)split * 2 * (size_t)p->n_s * sizeof(float);
+  const size_t y_bytes = (size_t)p->sep_n[1] * (size_t)std::max<int64_t>(p->n_slots, 1) * sizeof(float2);
+  const size_t z_bytes = (size_t)std::max<int64_t>(p->n_slots, 1) * (size_t)p->sep_n[2] * sizeof(float2);
+  const size_t part_bytes = (size_t)split * 2 * (size_t)p->sep_ns * sizeof(float);
   if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
   if ((e = cudaMalloc(&p->d.sep_Y, y_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Y");
   if ((e = cudaMalloc(&p->d.sep_Z, z_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Z");
   if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc separable partials");
-  p->base_bytes += (int64_t)(a_bytes + y_bytes + z_bytes + part_bytes);
+  if ((e = cudaMalloc(&p->d.sep_axis_s, alls.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
+  if ((e = cudaMalloc(&p->d.sep_axis64, all64.size() * sizeof(double))) != cudaSuccess) return cuda_status(e, "axes");
+  cudaMemcpy(p->d.sep_axis_s, alls.data(), alls.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d.sep_axis64, all64.data(), all64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  size_t virt_bytes = 0;
+  if (gid) {
+    virt_bytes = (size_t)p->sep_ns * sizeof(float2);
+    if ((e = cudaMalloc(&p->d.sep_virt, virt_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc virtual map");
+  }
+  p->base_bytes += (int64_t)(a_bytes + y_bytes + z_bytes + part_bytes + virt_bytes);
   if ((e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem)) != cudaSuccess)
     return cuda_status(e, "separable shared memory attribute");
   return SCATTER_OK;
@@ -508,10 +550,10 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   SepTabArgs t{};
   t.atom4 = p->d.atom4;
   t.atom_w = p->d.atom_w;
-  t.axis_s = p->d.axis_s;
-  t.n0 = p->n_axis[0];
-  t.n1 = p->n_axis[1];
-  t.n2 = p->n_axis[2];
+  t.axis_s = p->d.sep_axis_s;
+  t.n0 = p->sep_n[0];
+  t.n1 = p->sep_n[1];
+  t.n2 = p->sep_n[2];
   t.n_slots = p->n_slots;
   t.n_steps = p->sep_steps;
   t.n_mt = p->sep_mt;
@@ -522,7 +564,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   if (p->n_slots > 0) {
     const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;  // real tiles; a padding tile is never read
     k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
-    const int64_t nyz = p->n_axis[1] * p->n_slots + p->n_slots * p->n_axis[2];
+    const int64_t nyz = p->sep_n[1] * p->n_slots + p->n_slots * p->sep_n[2];
     k_sep_tab_yz<<<(unsigned)((nyz + 255) / 256), 256, 0, st>>>(t);
     p->last_launches += 2;
   }
@@ -533,11 +575,11 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
   a.coef = p->d.coef;
-  a.axis_s = p->d.axis_s;
-  a.n0 = p->n_axis[0];
-  a.n1 = p->n_axis[1];
-  a.n2 = p->n_axis[2];
-  a.n_s = p->n_s;
+  a.axis_s = p->d.sep_axis_s;
+  a.n0 = p->sep_n[0];
+  a.n1 = p->sep_n[1];
+  a.n2 = p->sep_n[2];
+  a.n_s = p->sep_ns;
   a.n_slots = p->n_slots;
   a.n_steps = p->sep_steps;
   a.n_mt = p->sep_mt;
@@ -551,10 +593,16 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
   timing_end(p, st);
   p->last_launches += 1;
-  k_sep_reduce<<<(unsigned)((p->n_s + 255) / 256), 256, 0, st>>>(
-      p->d.sep_partial, std::max(n_chunks, 1), p->n_s, p->d.axis64, p->n_axis[0], p->n_axis[1], p->n_axis[2],
-      p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, amp_out, int_out);
+  const bool gid = p->s_kind == SCATTER_S_GID_GRID;
+  k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
+      p->d.sep_partial, std::max(n_chunks, 1), p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
+      p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, gid ? p->d.sep_virt : amp_out,
+      gid ? nullptr : int_out);
   p->last_launches += 1;
+  if (gid) {
+    scatter_status s2 = launch_gid_combine(p, amp_out, int_out, st);
+    if (s2 != SCATTER_OK) return s2;
+  }
   return cuda_status(cudaGetLastError(), "separable launch");
 }
 
