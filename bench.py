@@ -206,7 +206,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     import __graft_entry__
-    from paper_1010_2641_gb300 import api
+    from paper_1010_2641_gb300 import api, sharding
 
     __graft_entry__.build()
     torch.cuda.set_device(local_rank)
@@ -255,9 +255,7 @@ def run_gpu(args, rank, world, local_rank):
     t_step = float(np.mean(step_ms))
     t_kern = float(np.mean(kern_ms))
     if world > 1:
-        t = torch.tensor([t_step, t_kern], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step, t_kern = t.tolist()
+        t_step, t_kern = sharding.max_over_ranks([t_step, t_kern], device=dev)
     value = world * pairs / (t_step * 1e-3)
 
     # ---- end to end through the public API with host buffers -------------------
@@ -283,9 +281,7 @@ def run_gpu(args, rank, world, local_rank):
         e2e_ms.append(e0.elapsed_time(e1))
     t_e2e = float(np.mean(e2e_ms))
     if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = t.item()
+        (t_e2e,) = sharding.max_over_ranks([t_e2e], device=dev)
 
     # ---- roofline of the dominant kernel ----------------------------------------
     sm_mhz = clk["sm_mhz"] if clk else None
