@@ -230,8 +230,6 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.gid_w64);
   release(d.ztab);
   release(d.sep_A);
-  release(d.sep_Y);
-  release(d.sep_Z);
   release(d.sep_partial);
   release(d.sep_axis_s);
   release(d.sep_axis64);

@@ -111,8 +111,6 @@ struct DeviceBuffers {
   float4* ztab = nullptr;           // [n_afb][n_slots][32] Z1, Z2 per call
   // separable path
   void* sep_A = nullptr;            // A operand blocks (f16 hi/lo)
-  float2* sep_Y = nullptr;          // [n1][n_slots]
-  float2* sep_Z = nullptr;          // [n_slots][n2]
   float* sep_partial = nullptr;     // [split][2][sep_ns] planar
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
   double* sep_axis64 = nullptr;     // separable grid axes, full S

@@ -1,30 +1,36 @@
 // Separable tensor-core path for axis-aligned S grids (tcgen05, sm_103a).
 //
 // On a grid S = H + (s_a, s_b, s_c) the phase of Eq. 2 separates,
-//   exp(2 i pi (c_j + s_a x'_j + s_b y'_j + s_c z'_j)) = X[a,j] Y[b,j] Zw[c,j] / w_j
-// with X = e^{2 pi i s_a x'}, Y = e^{2 pi i s_b y'}, Zw = w e^{2 pi i (c + s_c z')},
+//   w_j exp(2 i pi (c_j + s_a x'_j + s_b y'_j + s_c z'_j)) = Xw[a,j] B[(b,c),j]
+// with Xw = w e^{2 pi i s_a x'} and B = e^{2 pi i (s_b y' + s_c z' + c)},
 // so the per-species sum is a complex matrix product over the atoms:
-//   T_s[a, (b,c)] = sum_{j in s} X[a,j] B[(b,c), j],   B = Y[b,j] Zw[c,j].
+//   T_s[a, (b,c)] = sum_{j in s} Xw[a,j] B[(b,c), j].
 // It runs as a real GEMM D = A B^T on the 5th-generation tensor cores:
 //   A  (M = 2 n_a rows: Re/Im of each a) x (K = 2 per atom: Re/Im):
-//      rows 2a: [Xr, -Xi], rows 2a+1: [Xi, Xr]  -> D[2a] = Re T, D[2a+1] = Im T
+//      rows 2a: [Xwr, -Xwi], rows 2a+1: [Xwi, Xwr]  -> D[2a] = Re T, D[2a+1] = Im T
 //   B  (N = (b,c) points) x (K): [Br, Bi]
 // Both operands are split into f16 hi + lo parts and three products
 // (hi.hi + hi.lo + lo.hi) accumulate in FP32 in tensor memory (TMEM), which
 // keeps the result near FP32 accuracy (the lo.lo term is below 2^-22).
 //
-// Per call: k_sep_tables writes the A operand (hi/lo, already in the
+// Per call: k_sep_tab_a writes the A operand (hi/lo, already in the
 // canonical no-swizzle K-major shared-memory layout, one 16 KB block per
-// (M tile, 16-atom step), the two tiles of a pair adjacent) and the Y, Zw
-// tables.  k_sep: CTA = a pair of 128-row M tiles (two 128 x 256 FP32
+// (M tile, 16-atom step), the two tiles of a pair adjacent).
+// k_sep: CTA = a pair of 128-row M tiles (two 128 x 256 FP32
 // accumulators filling the 512 TMEM columns) x one 256-point N tile x one
-// atom chunk; per 16-atom step the TMA engine copies the pair's A blocks,
-// all threads form the B block (complex products, f16 split) in shared
-// memory once for both tiles, and one thread issues 12 tcgen05.mma
-// (2 tiles x 2 K16 sub-steps x 3 products, M=128 N=256).  A four-stage ring for the
-// A blocks (the TMA runs two steps ahead), a two-stage ring for the B blocks
-// and register prefetch of the next step's Y, Zw values keep the formation
-// of step k+1 overlapped with the MMAs of step k.
+// atom chunk; per 16-atom step the TMA engine copies the pair's A blocks
+// and the step's 16 atom records (y', z', c), every thread computes its
+// point's row of B from them (FP32 phase, exact reduction mod 1, MUFU
+// sincos, f16 split) into shared memory once for both tiles, and one
+// thread issues 12 tcgen05.mma (2 tiles x 2 K16 sub-steps x 3 products,
+// M=128 N=256).  A four-stage ring for the A blocks (the TMA runs two
+// steps ahead: the A stream is re-read from L2 by every N tile), an
+// eight-stage ring for the atom records (six steps ahead) and a two-stage
+// ring for the B blocks keep the formation of step k+1 overlapped with the
+// MMAs of step k.  The MMAs read ~96 B/clk of shared memory on their own;
+// computing B from the atom records, instead of loading tabulated factors
+// through L1, keeps the rest of the shared-memory traffic to the A copies
+// and the B stores.
 // Every 256 steps and at every species boundary the accumulator is read
 // from TMEM (tcgen05.ld), multiplied by f_s(|S|) and added into planar FP32
 // partials owned by the CTA; k_sep_reduce sums the chunks in order and
@@ -40,7 +46,8 @@
 
 namespace scatter {
 
-constexpr int kSepThreads = 256;
+constexpr int kSepFormWarps = 8;           // warps forming B rows (one point per thread)
+constexpr int kSepThreads = 32 * (kSepFormWarps + 1);  // + the MMA / copy warp
 constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
 constexpr int kSepN = 256;                 // MMA N (points per CTA)
 constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
@@ -48,8 +55,11 @@ constexpr int kSepFlush = 256;             // steps between TMEM flushes
 constexpr uint32_t kSepABytes = 16384;     // A block of one M tile: hi + lo, 128 x 32 f16 each
 constexpr int kSepPair = 2;                // M tiles per CTA (one formed B tile feeds both)
 constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
-constexpr int kSepAStages = 4;             // A ring: TMA runs two steps ahead
+constexpr int kSepAStages = 4;             // A ring: the TMA runs kSepAhead steps ahead
+constexpr int kSepAhead = 2;               // the stage it refills was last read by step g-2
 constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
+constexpr int kSepTStages = 8;             // atom-record ring (256 B per step)
+constexpr int kSepTAhead = 6;              // its stage is refilled once step g-2 passed the CTA barrier
 constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
 constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
 
@@ -120,12 +130,10 @@ struct SepTabArgs {
   int64_t n0, n1, n2;
   int64_t n_slots, n_steps, n_mt;
   uint4* A;             // [n_mt/2][n_steps][2 tiles][hi|lo][4 kb][16 mg][8 rows] of 16 B
-  float2* Y;            // [n1][n_slots]
-  float2* Zw;           // [n_slots][n2]
 };
 
 // One thread per 16-byte row of a core matrix of the A operand (4 atoms x
-// Re/Im of one row m), hi and lo parts.
+// Re/Im of one row m), hi and lo parts; the weight w_j is folded in here.
 __global__ void k_sep_tab_a(const SepTabArgs t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = t.n_mt * t.n_steps * 4 * kSepM;
@@ -144,6 +152,9 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
     if (a < t.n0) {
       const float p = sa * t.atom4[slot].x;
       sincospif(2.0f * (p - rintf(p)), &sn, &cs);
+      const float w = t.atom_w[slot];
+      sn *= w;
+      cs *= w;
     }
     // row 2a: (Xr, -Xi); row 2a+1: (Xi, Xr)
     v[2 * q] = ri ? sn : cs;
@@ -160,34 +171,13 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
   blk[512 + off] = lo;
 }
 
-__global__ void k_sep_tab_yz(const SepTabArgs t) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ny = t.n1 * t.n_slots, nz = t.n_slots * t.n2;
-  if (i < ny) {
-    const int64_t b = i / t.n_slots, slot = i % t.n_slots;
-    const float p = t.axis_s[t.n0 + b] * t.atom4[slot].y;
-    float sn, cs;
-    sincospif(2.0f * (p - rintf(p)), &sn, &cs);
-    t.Y[i] = make_float2(cs, sn);
-  } else if (i < ny + nz) {
-    const int64_t k = i - ny, slot = k / t.n2, c = k % t.n2;
-    const float4 at = t.atom4[slot];
-    const float p = fmaf(t.axis_s[t.n0 + t.n1 + c], at.z, at.w);
-    float sn, cs;
-    sincospif(2.0f * (p - rintf(p)), &sn, &cs);
-    const float w = t.atom_w[slot];
-    t.Zw[k] = make_float2(w * cs, w * sn);
-  }
-}
-
 // -------------------------------------------------------------------------
 // main kernel
 // -------------------------------------------------------------------------
 
 struct SepArgs {
   const uint4* A;
-  const float2* Y;
-  const float2* Zw;
+  const float4* atom4;  // per slot (x', y', z', c)
   const Segment* segs;
   const int32_t* chunk_seg_off;
   const float* coef;
@@ -200,30 +190,70 @@ struct SepArgs {
   unsigned* status;
 };
 
-__global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
+// Accumulation groups: the steps between two TMEM flushes (every kSepFlush
+// steps and at every species boundary).  Both roles walk them identically.
+struct SepGroups {
+  int cur_seg, seg_hi;
+  int64_t seg_end_ks, grp_start;
+  __device__ bool ends_at(int64_t ks) const { return ks + 1 == seg_end_ks || ks + 1 - grp_start >= kSepFlush; }
+  __device__ void advance(int64_t ks, const Segment* segs) {  // past the group ending at ks
+    const bool seg_done = ks + 1 == seg_end_ks;
+    grp_start = ks + 1;
+    if (seg_done && ++cur_seg < seg_hi) seg_end_ks = segs[cur_seg].end / kSepStep;
+  }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(dev::smem_addr(bar)) : "memory");
+}
+
+// Warp roles: warps 0..7 form the B rows (one point per thread) and read the
+// accumulators out at every group end; warp 8 (one lane) issues the TMA
+// copies and the MMAs.  Hand-offs go through mbarriers only, so issuing the
+// MMAs never holds up the formation of the next step:
+//   bar_full[a]  A block of a step arrived          (TMA, 1 arrival + bytes)
+//   bar_atom[t]  atom records of a step arrived     (TMA)
+//   bar_bfull[b] B block of a step formed           (8 warps)
+//   bar_mma[b]   MMAs of the step done (commit); frees its B and A stages
+//   bar_tfree    accumulators read out after a group end (8 warps)
+__global__ void __maxnreg__(168) k_sep(const SepArgs a) {
+  static_assert(kSepAStages - kSepAhead <= kSepBStages, "A-stage reuse is tracked on the B-stage barriers");
+  static_assert(kSepTAhead < kSepTStages, "atom ring depth");
   extern __shared__ __align__(1024) unsigned char sep_smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kSepAStages];
+  __shared__ __align__(8) uint64_t bar_atom[kSepTStages];
+  __shared__ __align__(8) uint64_t bar_bfull[kSepBStages];
   __shared__ __align__(8) uint64_t bar_mma[kSepBStages];
+  __shared__ __align__(8) uint64_t bar_tfree;
+  __shared__ __align__(16) float4 ring_atom[kSepTStages][kSepStep];
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(sep_smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* ringA = smem;
   unsigned char* ringB = smem + kSepAStages * kSepPair * kSepABytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == kSepFormWarps;
   const int64_t n_mp = (a.n_mt + 1) / 2;
   const int64_t mp = blockIdx.x % n_mp, nt = blockIdx.x / n_mp;
   const int ntp = 2 * mp + 1 < a.n_mt ? 2 : 1;  // M tiles of this CTA with rows
   const int chunk = blockIdx.y;
   const int64_t nbc = a.n1 * a.n2;
 
-  if (warp == 0) {
+  if (mma_warp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dev::smem_addr(&tmem_slot)),
                  "r"(kSepTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     for (int s = 0; s < kSepAStages; ++s) dev::mbar_init(&bar_full[s], 1);
-    for (int s = 0; s < kSepBStages; ++s) dev::mbar_init(&bar_mma[s], 1);
+    for (int s = 0; s < kSepTStages; ++s) dev::mbar_init(&bar_atom[s], 1);
+    for (int s = 0; s < kSepBStages; ++s) {
+      dev::mbar_init(&bar_bfull[s], kSepFormWarps);
+      dev::mbar_init(&bar_mma[s], 1);
+    }
+    dev::mbar_init(&bar_tfree, kSepFormWarps);
+    s_abort = 0;
     dev::mbar_fence_init();
   }
   tc_fence_before();
@@ -231,85 +261,67 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // this thread's B row: point bc of the N tile
-  const int64_t bc = nt * kSepN + tid;
-  const bool row_ok = bc < nbc;
-  const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
-  const float2* Yrow = a.Y + rb * a.n_slots;
-  const float2* Zcol = a.Zw + rc;
-  const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
-
   const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
-  const uint4* Ablk = a.A + mp * a.n_steps * (kSepPair * kSepABytes / 16);
-  float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
-  float* part_im = part_re + a.n_s;
   // the chunk's steps are contiguous; species boundaries fall on step edges
   const int64_t ks_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin / kSepStep : 0;
   const int64_t ks_end = seg_lo < seg_hi ? a.segs[seg_hi - 1].end / kSepStep : 0;
-
-  auto issue_a = [&](int64_t ks, int64_t g) {
-    const int st = (int)(g & (kSepAStages - 1));
-    const uint32_t bytes = (uint32_t)ntp * kSepABytes;
-    dev::mbar_arrive_expect_tx(&bar_full[st], bytes);
-    dev::bulk_g2s(ringA + st * kSepPair * kSepABytes, Ablk + ks * (kSepPair * kSepABytes / 16), bytes, &bar_full[st]);
-  };
-  auto load_yz = [&](int64_t ks, float2 (&y)[kSepStep], float2 (&z)[kSepStep]) {
-    const int64_t slot0 = ks * kSepStep;
-#pragma unroll
-    for (int q = 0; q < kSepStep; ++q) {
-      y[q] = row_ok ? __ldg(Yrow + slot0 + q) : make_float2(0.f, 0.f);
-      z[q] = row_ok ? __ldg(Zcol + (slot0 + q) * a.n2) : make_float2(0.f, 0.f);
-    }
-  };
-  if (tid == 0) {
-    for (int d = 0; d < 2; ++d)
-      if (ks_begin + d < ks_end) issue_a(ks_begin + d, d);
-  }
-  float2 cy[kSepStep], cz[kSepStep];
-  if (ks_begin < ks_end) load_yz(ks_begin, cy, cz);
-
-  int64_t g = 0;  // steps issued by this CTA
+  SepGroups grp{seg_lo, seg_hi, seg_lo < seg_hi ? a.segs[seg_lo].end / kSepStep : 0, ks_begin};
   bool ok = true;
-  bool first_flush = true;
-  int cur_seg = seg_lo;
-  int64_t seg_end_ks = seg_lo < seg_hi ? a.segs[seg_lo].end / kSepStep : 0;
-  int64_t grp_start = ks_begin;
+  // MMA lane: copies issued (steps) and steps committed, for the drain on abort
+  int64_t a_issued = 0, t_issued = 0, g_committed = 0;
 
-  for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
-    const int bst = (int)(g & (kSepBStages - 1));
-    const int ast = (int)(g & (kSepAStages - 1));
-    unsigned char* sB = ringB + bst * kSepBBytes;
-    // B stage bst and A stage of step g-2 are free once the MMAs of g-2 completed
-    bool w_ok = true;
-    if (g >= 2) w_ok = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)(((g - 2) >> 1) & 1));
-    if (tid == 0 && w_ok && ks + 2 < ks_end) issue_a(ks + 2, g + 2);
-    // prefetch the next step's Y, Zw into registers, then form this step's B
-    float2 ny[kSepStep], nz[kSepStep];
-    if (ks + 1 < ks_end) load_yz(ks + 1, ny, nz);
-    if (w_ok) {
-#pragma unroll
-      for (int kb = 0; kb < 4; ++kb) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 y = cy[kb * 4 + q], z = cz[kb * 4 + q];
-          split2(fmaf(y.x, z.x, -y.y * z.y), fmaf(y.x, z.y, y.y * z.x), hi[q], lo[q]);
+  if (mma_warp) {
+    if (lane == 0) {
+      const uint4* Ablk = a.A + mp * a.n_steps * (kSepPair * kSepABytes / 16);
+      auto issue_a = [&](int64_t ks, int64_t g) {
+        const int st = (int)(g % kSepAStages);
+        const uint32_t bytes = (uint32_t)ntp * kSepABytes;
+        a_issued = g + 1;
+        dev::mbar_arrive_expect_tx(&bar_full[st], bytes);
+        dev::bulk_g2s(ringA + st * kSepPair * kSepABytes, Ablk + ks * (kSepPair * kSepABytes / 16), bytes,
+                      &bar_full[st]);
+      };
+      auto issue_atoms = [&](int64_t ks, int64_t g) {
+        const int st = (int)(g % kSepTStages);
+        t_issued = g + 1;
+        dev::mbar_arrive_expect_tx(&bar_atom[st], kSepStep * sizeof(float4));
+        dev::bulk_g2s(&ring_atom[st][0], a.atom4 + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[st]);
+      };
+      for (int d = 0; d < kSepAhead; ++d)
+        if (ks_begin + d < ks_end) issue_a(ks_begin + d, d);
+      for (int d = 0; d < kSepTAhead; ++d)
+        if (ks_begin + d < ks_end) issue_atoms(ks_begin + d, d);
+      int64_t flushes = 0;  // groups read out before the current one
+      int64_t g = 0;
+      for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
+        if (s_abort) {
+          ok = false;
+          break;
         }
-        *reinterpret_cast<uint4*>(sB + kb * 4096 + b_row_off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (__syncthreads_or(!w_ok)) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g >> 2) & 1))) {
-        dev::set_status(a.status, kStatusTimeout);
-      } else {
+        // the A stage of step g + kSepAhead was last read by the MMAs of step
+        // g + kSepAhead - kSepAStages
+        const int64_t ga = g + kSepAhead - kSepAStages;
+        if (ga >= 0 && !dev::mbar_wait_bounded(&bar_mma[ga % kSepBStages], (uint32_t)((ga / kSepBStages) & 1))) {
+          ok = false;
+          break;
+        }
+        if (ks + kSepAhead < ks_end) issue_a(ks + kSepAhead, g + kSepAhead);
+        // the atom stage of step g + kSepTAhead was read by the formation of a
+        // step (< g) whose B block this lane already waited for
+        if (ks + kSepTAhead < ks_end) issue_atoms(ks + kSepTAhead, g + kSepTAhead);
+        if (ks == grp.grp_start && flushes > 0 &&
+            !dev::mbar_wait_bounded(&bar_tfree, (uint32_t)((flushes - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const int ast = (int)(g % kSepAStages), bst = (int)(g % kSepBStages);
+        if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g / kSepAStages) & 1)) ||
+            !dev::mbar_wait_bounded(&bar_bfull[bst], (uint32_t)((g / kSepBStages) & 1))) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const uint32_t aB = dev::smem_addr(sB);
+        const uint32_t aB = dev::smem_addr(ringB + bst * kSepBBytes);
         for (int tp = 0; tp < ntp; ++tp) {
           const uint32_t aA = dev::smem_addr(ringA + (ast * kSepPair + tp) * kSepABytes);
           const uint32_t d = tmem + (uint32_t)(tp * kSepN);
@@ -319,108 +331,166 @@ __global__ void __launch_bounds__(kSepThreads, 1) k_sep(const SepArgs a) {
             const uint64_t a_lo = smem_desc(aA + 8192 + u * 4096, 2048, 128);
             const uint64_t b_hi = smem_desc(aB + u * 8192, 4096, 128);
             const uint64_t b_lo = smem_desc(aB + 16384 + u * 8192, 4096, 128);
-            const uint32_t acc0 = (ks > grp_start || u > 0) ? 1u : 0u;
+            const uint32_t acc0 = (ks > grp.grp_start || u > 0) ? 1u : 0u;
             mma_f16(d, a_hi, b_hi, acc0);
             mma_f16(d, a_hi, b_lo, 1u);
             mma_f16(d, a_lo, b_hi, 1u);
           }
         }
+        mma_commit(&bar_mma[bst]);
+        g_committed = g + 1;
+        if (grp.ends_at(ks)) {
+          grp.advance(ks, a.segs);
+          ++flushes;
+        }
       }
-      mma_commit(&bar_mma[bst]);
     }
+  } else {
+    // ---- formation warps ---------------------------------------------------
+    // this thread's B row: point bc of the N tile, offsets (s_b, s_c) from H
+    const int64_t bc = nt * kSepN + tid;
+    const bool row_ok = bc < nbc;
+    const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
+    const float sb = a.axis_s[a.n0 + rb], sc = a.axis_s[a.n0 + a.n1 + rc];
+    const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+    float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
+    float* part_im = part_re + a.n_s;
+    bool first_flush = true;
+    int64_t g = 0;
+    for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
+      const int bst = (int)(g % kSepBStages), tst = (int)(g % kSepTStages);
+      // B stage bst is free once the MMAs of step g - kSepBStages completed;
+      // every lane waits, the warp agrees on the outcome
+      bool w = !s_abort;
+      if (w && g >= kSepBStages)
+        w = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)(((g - kSepBStages) / kSepBStages) & 1));
+      if (w) w = dev::mbar_wait_bounded(&bar_atom[tst], (uint32_t)((g / kSepTStages) & 1));
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        break;
+      }
+      // B[(b,c), j] = e^{2 pi i (s_b y'_j + s_c z'_j + c_j)}, zero past the last point
+      unsigned char* sB = ringB + bst * kSepBBytes;
+      const float4* at = ring_atom[tst];
 #pragma unroll
-    for (int q = 0; q < kSepStep; ++q) {
-      cy[q] = ny[q];
-      cz[q] = nz[q];
-    }
-    const bool seg_done = ks + 1 == seg_end_ks;
-    if (!seg_done && ks + 1 - grp_start < kSepFlush) continue;
-
-    // ---- flush: TMEM -> f_s(|S|) x T -> planar partials --------------------
-    const bool d_ok = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)((g >> 1) & 1));
-    if (__syncthreads_or(!d_ok)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    const float* cf = a.coef + kNCoef * a.segs[cur_seg].species;
-    const int sub = warp & 3;
-    const int col0 = (warp >> 2) * 128;
-    for (int tp = 0; tp < ntp; ++tp) {
-      const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;  // A row = 2a + ri
-      const int64_t pa = m_row >> 1;
-      const bool is_im = (m_row & 1) != 0;
-      const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
-  #pragma unroll 1
-      for (int cc = 0; cc < 128; cc += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
-        const int64_t bc0 = nt * kSepN + col0 + cc;
-        int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
-        float res[32];
-  #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
-          const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
-          const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
-          const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
-          const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
-          const float2 F = dev::form_factor(cf, s2);
-          res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
-          if (++ic == a.n2) {
-            ic = 0;
-            ++ib;
+      for (int kb = 0; kb < 4; ++kb) {
+        uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
+        if (row_ok) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 v = at[kb * 4 + q];
+            const float ph = dev::frac_rn(fmaf(sb, v.y, fmaf(sc, v.z, v.w)));
+            float sn, cs;
+            dev::sincos_cycles_mufu(ph, &sn, &cs);
+            split2(cs, sn, hi[q], lo[q]);
           }
         }
-        if (pa < a.n0 && bc0 < nbc) {
-          float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
-          if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-  #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
-              o.x += res[4 * q];
-              o.y += res[4 * q + 1];
-              o.z += res[4 * q + 2];
-              o.w += res[4 * q + 3];
-              d4[q] = o;
+        *reinterpret_cast<uint4*>(sB + kb * 4096 + b_row_off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_bfull[bst]);
+      if (!grp.ends_at(ks)) continue;
+
+      // ---- group end: TMEM -> f_s(|S|) x T -> planar partials ---------------
+      // the commit of step g covers every earlier MMA of the group
+      w = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)((g / kSepBStages) & 1));
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const float* cf = a.coef + kNCoef * a.segs[grp.cur_seg].species;
+      const int sub = warp & 3;
+      const int col0 = (warp >> 2) * 128;
+      for (int tp = 0; tp < ntp; ++tp) {
+        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;  // A row = 2a + ri
+        const int64_t pa = m_row >> 1;
+        const bool is_im = (m_row & 1) != 0;
+        const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
+#pragma unroll 1
+        for (int cc = 0; cc < 128; cc += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
+          const int64_t bc0 = nt * kSepN + col0 + cc;
+          int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
+          float res[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
+            const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
+            const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
+            const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
+            const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
+            const float2 F = dev::form_factor(cf, s2);
+            res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
+            if (++ic == a.n2) {
+              ic = 0;
+              ++ib;
             }
-          } else {
-  #pragma unroll
-            for (int q = 0; q < 32; ++q)
-              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+          }
+          if (pa < a.n0 && bc0 < nbc) {
+            float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
+            if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+              float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
+                o.x += res[4 * q];
+                o.y += res[4 * q + 1];
+                o.z += res[4 * q + 2];
+                o.w += res[4 * q + 3];
+                d4[q] = o;
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < 32; ++q)
+                if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+            }
           }
         }
       }
+      first_flush = false;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_tfree);
+      grp.advance(ks, a.segs);
     }
-    first_flush = false;
-    tc_fence_before();
-    __syncthreads();
-    grp_start = ks + 1;
-    if (seg_done && ++cur_seg < seg_hi) seg_end_ks = a.segs[cur_seg].end / kSepStep;
-  }
-  if (ok && first_flush) {
-    // empty chunk: its partials are zero
-    const int sub = warp & 3;
-    const int col0 = (warp >> 2) * 128;
-    for (int tp = 0; tp < ntp; ++tp) {
-      const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
-      const int64_t pa = m_row >> 1;
-      if (pa < a.n0) {
-        float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
-        for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+    if (ok && first_flush) {
+      // empty chunk: its partials are zero
+      const int sub = warp & 3;
+      const int col0 = (warp >> 2) * 128;
+      for (int tp = 0; tp < ntp; ++tp) {
+        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
+        const int64_t pa = m_row >> 1;
+        if (pa < a.n0) {
+          float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
+          for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+        }
       }
     }
   }
   if (!ok) {
+    s_abort = 1;
     dev::set_status(a.status, kStatusTimeout);
-    // wait (bounded) for MMAs still in flight before releasing TMEM
-    if (tid == 0 && g > 0)
-      dev::mbar_wait_bounded(&bar_mma[(g - 1) & (kSepBStages - 1)], (uint32_t)(((g - 1) >> 1) & 1), 1LL << 28);
+  }
+  __syncthreads();
+  if (mma_warp && lane == 0 && s_abort) {
+    // wait (bounded) for MMAs and copies still in flight before releasing
+    // TMEM and shared memory; phases already complete return at once
+    if (g_committed > 0) {
+      const int64_t gl = g_committed - 1;
+      dev::mbar_wait_bounded(&bar_mma[gl % kSepBStages], (uint32_t)((gl / kSepBStages) & 1), 1LL << 28);
+    }
+    for (int64_t s = a_issued > kSepAStages ? a_issued - kSepAStages : 0; s < a_issued; ++s)
+      dev::mbar_wait_bounded(&bar_full[s % kSepAStages], (uint32_t)((s / kSepAStages) & 1), 1LL << 28);
+    for (int64_t s = t_issued > kSepTStages ? t_issued - kSepTStages : 0; s < t_issued; ++s)
+      dev::mbar_wait_bounded(&bar_atom[s % kSepTStages], (uint32_t)((s / kSepTStages) & 1), 1LL << 28);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSepTmemCols));
+  if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSepTmemCols));
 }
 
 // Sum of the planar chunk partials in order, translation phase, outputs.
@@ -523,12 +593,8 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   p->sep_steps = n_steps;
   cudaError_t e;
   const size_t a_bytes = (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
-  const size_t y_bytes = (size_t)p->sep_n[1] * (size_t)std::max<int64_t>(p->n_slots, 1) * sizeof(float2);
-  const size_t z_bytes = (size_t)std::max<int64_t>(p->n_slots, 1) * (size_t)p->sep_n[2] * sizeof(float2);
   const size_t part_bytes = (size_t)split * 2 * (size_t)p->sep_ns * sizeof(float);
   if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
-  if ((e = cudaMalloc(&p->d.sep_Y, y_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Y");
-  if ((e = cudaMalloc(&p->d.sep_Z, z_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable Z");
   if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc separable partials");
   if ((e = cudaMalloc(&p->d.sep_axis_s, alls.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
@@ -540,7 +606,8 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     virt_bytes = (size_t)p->sep_ns * sizeof(float2);
     if ((e = cudaMalloc(&p->d.sep_virt, virt_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc virtual map");
   }
-  p->base_bytes += (int64_t)(a_bytes + y_bytes + z_bytes + part_bytes + virt_bytes);
+  p->base_bytes += (int64_t)(a_bytes + part_bytes + virt_bytes);
+  static_assert(kSepSmem + 4096 <= 227 * 1024, "dynamic + static shared memory of k_sep");
   if ((e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem)) != cudaSuccess)
     return cuda_status(e, "separable shared memory attribute");
   return SCATTER_OK;
@@ -558,20 +625,15 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   t.n_steps = p->sep_steps;
   t.n_mt = p->sep_mt;
   t.A = static_cast<uint4*>(p->d.sep_A);
-  t.Y = p->d.sep_Y;
-  t.Zw = p->d.sep_Z;
   const int n_chunks = (int)p->chunk_seg_off.size() - 1;
   if (p->n_slots > 0) {
     const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;  // real tiles; a padding tile is never read
     k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
-    const int64_t nyz = p->sep_n[1] * p->n_slots + p->n_slots * p->sep_n[2];
-    k_sep_tab_yz<<<(unsigned)((nyz + 255) / 256), 256, 0, st>>>(t);
-    p->last_launches += 2;
+    p->last_launches += 1;
   }
   SepArgs a{};
   a.A = static_cast<const uint4*>(p->d.sep_A);
-  a.Y = p->d.sep_Y;
-  a.Zw = p->d.sep_Z;
+  a.atom4 = p->d.atom4;
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
   a.coef = p->d.coef;
