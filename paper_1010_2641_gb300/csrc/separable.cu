@@ -23,11 +23,13 @@
 // point's row of B from them (FP32 phase, exact reduction mod 1, MUFU
 // sincos, f16 split) into shared memory once for both tiles, and one
 // thread issues 12 tcgen05.mma (2 tiles x 2 K16 sub-steps x 3 products,
-// M=128 N=256).  A four-stage ring for the A blocks (the TMA runs two
-// steps ahead: the A stream is re-read from L2 by every N tile), an
-// eight-stage ring for the atom records (six steps ahead) and a two-stage
-// ring for the B blocks keep the formation of step k+1 overlapped with the
-// MMAs of step k.  The MMAs read ~96 B/clk of shared memory on their own;
+// M=128 N=256).  Warp roles: eight warps form B (and read the accumulators
+// out), one warp issues the MMAs, one warp issues the copies (a 32 KB bulk
+// copy holds its issuing thread for ~1000 cycles, so it must not be the MMA
+// thread).  A four-stage ring for the A blocks, an eight-stage ring for the
+// atom records and a two-stage ring for the B blocks, each stage with a
+// full and an empty mbarrier, keep the formation of step k+1 and the copies
+// of later steps overlapped with the MMAs of step k.  The MMAs read ~96 B/clk of shared memory on their own;
 // computing B from the atom records, instead of loading tabulated factors
 // through L1, keeps the rest of the shared-memory traffic to the A copies
 // and the B stores.
@@ -47,7 +49,7 @@
 namespace scatter {
 
 constexpr int kSepFormWarps = 8;           // warps forming B rows (one point per thread)
-constexpr int kSepThreads = 32 * (kSepFormWarps + 1);  // + the MMA / copy warp
+constexpr int kSepThreads = 32 * (kSepFormWarps + 2);  // + the MMA warp + the copy warp
 constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
 constexpr int kSepN = 256;                 // MMA N (points per CTA)
 constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
@@ -55,11 +57,9 @@ constexpr int kSepFlush = 256;             // steps between TMEM flushes
 constexpr uint32_t kSepABytes = 16384;     // A block of one M tile: hi + lo, 128 x 32 f16 each
 constexpr int kSepPair = 2;                // M tiles per CTA (one formed B tile feeds both)
 constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
-constexpr int kSepAStages = 4;             // A ring: the TMA runs kSepAhead steps ahead
-constexpr int kSepAhead = 2;               // the stage it refills was last read by step g-2
+constexpr int kSepAStages = 4;             // A ring (full / empty barrier per stage)
 constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
 constexpr int kSepTStages = 8;             // atom-record ring (256 B per step)
-constexpr int kSepTAhead = 6;              // its stage is refilled once step g-2 passed the CTA barrier
 constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
 constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
 
@@ -208,20 +208,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Warp roles: warps 0..7 form the B rows (one point per thread) and read the
-// accumulators out at every group end; warp 8 (one lane) issues the TMA
-// copies and the MMAs.  Hand-offs go through mbarriers only, so issuing the
-// MMAs never holds up the formation of the next step:
-//   bar_full[a]  A block of a step arrived          (TMA, 1 arrival + bytes)
-//   bar_atom[t]  atom records of a step arrived     (TMA)
-//   bar_bfull[b] B block of a step formed           (8 warps)
-//   bar_mma[b]   MMAs of the step done (commit); frees its B and A stages
-//   bar_tfree    accumulators read out after a group end (8 warps)
+// accumulators out at every group end; warp 8 (one lane) issues the MMAs;
+// warp 9 (one lane) issues the TMA copies.  Hand-offs go through mbarriers
+// only:
+//   bar_full[a]   A block of a step arrived            (TMA, 1 arrival + bytes)
+//   bar_aempty[a] MMAs that read the A stage done      (commit)
+//   bar_atom[t]   atom records of a step arrived       (TMA)
+//   bar_tempty[t] atom records read by the formation   (8 warps)
+//   bar_bfull[b]  B block of a step formed             (8 warps)
+//   bar_mma[b]    MMAs of the step done (commit); frees its B stage
+//   bar_tfree     accumulators read out after a group end (8 warps)
 __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
-  static_assert(kSepAStages - kSepAhead <= kSepBStages, "A-stage reuse is tracked on the B-stage barriers");
-  static_assert(kSepTAhead < kSepTStages, "atom ring depth");
   extern __shared__ __align__(1024) unsigned char sep_smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kSepAStages];
+  __shared__ __align__(8) uint64_t bar_aempty[kSepAStages];
   __shared__ __align__(8) uint64_t bar_atom[kSepTStages];
+  __shared__ __align__(8) uint64_t bar_tempty[kSepTStages];
   __shared__ __align__(8) uint64_t bar_bfull[kSepBStages];
   __shared__ __align__(8) uint64_t bar_mma[kSepBStages];
   __shared__ __align__(8) uint64_t bar_tfree;
@@ -233,7 +235,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   unsigned char* ringA = smem;
   unsigned char* ringB = smem + kSepAStages * kSepPair * kSepABytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool mma_warp = warp == kSepFormWarps;
+  const bool mma_warp = warp == kSepFormWarps, copy_warp = warp == kSepFormWarps + 1;
   const int64_t n_mp = (a.n_mt + 1) / 2;
   const int64_t mp = blockIdx.x % n_mp, nt = blockIdx.x / n_mp;
   const int ntp = 2 * mp + 1 < a.n_mt ? 2 : 1;  // M tiles of this CTA with rows
@@ -246,8 +248,14 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < kSepAStages; ++s) dev::mbar_init(&bar_full[s], 1);
-    for (int s = 0; s < kSepTStages; ++s) dev::mbar_init(&bar_atom[s], 1);
+    for (int s = 0; s < kSepAStages; ++s) {
+      dev::mbar_init(&bar_full[s], 1);
+      dev::mbar_init(&bar_aempty[s], 1);
+    }
+    for (int s = 0; s < kSepTStages; ++s) {
+      dev::mbar_init(&bar_atom[s], 1);
+      dev::mbar_init(&bar_tempty[s], kSepFormWarps);
+    }
     for (int s = 0; s < kSepBStages; ++s) {
       dev::mbar_init(&bar_bfull[s], kSepFormWarps);
       dev::mbar_init(&bar_mma[s], 1);
@@ -267,30 +275,43 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   const int64_t ks_end = seg_lo < seg_hi ? a.segs[seg_hi - 1].end / kSepStep : 0;
   SepGroups grp{seg_lo, seg_hi, seg_lo < seg_hi ? a.segs[seg_lo].end / kSepStep : 0, ks_begin};
   bool ok = true;
-  // MMA lane: copies issued (steps) and steps committed, for the drain on abort
+  // copies issued and MMA steps committed (steps), for the drain on abort
   int64_t a_issued = 0, t_issued = 0, g_committed = 0;
 
-  if (mma_warp) {
+  if (copy_warp) {
     if (lane == 0) {
+      // A block and atom records of every step, in step order; a stage is
+      // refilled once its previous contents were consumed
       const uint4* Ablk = a.A + mp * a.n_steps * (kSepPair * kSepABytes / 16);
-      auto issue_a = [&](int64_t ks, int64_t g) {
-        const int st = (int)(g % kSepAStages);
-        const uint32_t bytes = (uint32_t)ntp * kSepABytes;
-        a_issued = g + 1;
-        dev::mbar_arrive_expect_tx(&bar_full[st], bytes);
-        dev::bulk_g2s(ringA + st * kSepPair * kSepABytes, Ablk + ks * (kSepPair * kSepABytes / 16), bytes,
-                      &bar_full[st]);
-      };
-      auto issue_atoms = [&](int64_t ks, int64_t g) {
-        const int st = (int)(g % kSepTStages);
+      const uint32_t a_bytes = (uint32_t)ntp * kSepABytes;
+      int64_t g = 0;
+      for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
+        if (s_abort) {
+          ok = false;
+          break;
+        }
+        const int tst = (int)(g % kSepTStages), ast = (int)(g % kSepAStages);
+        if (g >= kSepTStages &&
+            !dev::mbar_wait_bounded(&bar_tempty[tst], (uint32_t)(((g - kSepTStages) / kSepTStages) & 1))) {
+          ok = false;
+          break;
+        }
+        dev::mbar_arrive_expect_tx(&bar_atom[tst], kSepStep * sizeof(float4));
+        dev::bulk_g2s(&ring_atom[tst][0], a.atom4 + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
         t_issued = g + 1;
-        dev::mbar_arrive_expect_tx(&bar_atom[st], kSepStep * sizeof(float4));
-        dev::bulk_g2s(&ring_atom[st][0], a.atom4 + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[st]);
-      };
-      for (int d = 0; d < kSepAhead; ++d)
-        if (ks_begin + d < ks_end) issue_a(ks_begin + d, d);
-      for (int d = 0; d < kSepTAhead; ++d)
-        if (ks_begin + d < ks_end) issue_atoms(ks_begin + d, d);
+        if (g >= kSepAStages &&
+            !dev::mbar_wait_bounded(&bar_aempty[ast], (uint32_t)(((g - kSepAStages) / kSepAStages) & 1))) {
+          ok = false;
+          break;
+        }
+        dev::mbar_arrive_expect_tx(&bar_full[ast], a_bytes);
+        dev::bulk_g2s(ringA + ast * kSepPair * kSepABytes, Ablk + ks * (kSepPair * kSepABytes / 16), a_bytes,
+                      &bar_full[ast]);
+        a_issued = g + 1;
+      }
+    }
+  } else if (mma_warp) {
+    if (lane == 0) {
       int64_t flushes = 0;  // groups read out before the current one
       int64_t g = 0;
       for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -298,17 +319,6 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           ok = false;
           break;
         }
-        // the A stage of step g + kSepAhead was last read by the MMAs of step
-        // g + kSepAhead - kSepAStages
-        const int64_t ga = g + kSepAhead - kSepAStages;
-        if (ga >= 0 && !dev::mbar_wait_bounded(&bar_mma[ga % kSepBStages], (uint32_t)((ga / kSepBStages) & 1))) {
-          ok = false;
-          break;
-        }
-        if (ks + kSepAhead < ks_end) issue_a(ks + kSepAhead, g + kSepAhead);
-        // the atom stage of step g + kSepTAhead was read by the formation of a
-        // step (< g) whose B block this lane already waited for
-        if (ks + kSepTAhead < ks_end) issue_atoms(ks + kSepTAhead, g + kSepTAhead);
         if (ks == grp.grp_start && flushes > 0 &&
             !dev::mbar_wait_bounded(&bar_tfree, (uint32_t)((flushes - 1) & 1))) {
           ok = false;
@@ -338,6 +348,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           }
         }
         mma_commit(&bar_mma[bst]);
+        mma_commit(&bar_aempty[ast]);
         g_committed = g + 1;
         if (grp.ends_at(ks)) {
           grp.advance(ks, a.segs);
@@ -390,7 +401,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_bfull[bst]);
+      if (lane == 0) {
+        mbar_arrive(&bar_bfull[bst]);
+        mbar_arrive(&bar_tempty[tst]);
+      }
       if (!grp.ends_at(ks)) continue;
 
       // ---- group end: TMEM -> f_s(|S|) x T -> planar partials ---------------
@@ -411,9 +425,17 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
+          const int64_t bc0 = nt * kSepN + col0 + cc;
+          float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
+          const bool row_in = pa < a.n0 && bc0 < nbc;
+          const bool vec = row_in && bc0 + 32 <= nbc && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+          // the partials' loads go out before the TMEM read and the form factors
+          float4 old[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            old[q] = (vec && !first_flush) ? reinterpret_cast<const float4*>(dst)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
-          const int64_t bc0 = nt * kSepN + col0 + cc;
           int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
           float res[32];
 #pragma unroll
@@ -430,24 +452,16 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
               ++ib;
             }
           }
-          if (pa < a.n0 && bc0 < nbc) {
-            float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
-            if (bc0 + 32 <= nbc && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-              float4* d4 = reinterpret_cast<float4*>(dst);
+          if (vec) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                float4 o = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[q];
-                o.x += res[4 * q];
-                o.y += res[4 * q + 1];
-                o.z += res[4 * q + 2];
-                o.w += res[4 * q + 3];
-                d4[q] = o;
-              }
-            } else {
+            for (int q = 0; q < 8; ++q)
+              d4[q] = make_float4(old[q].x + res[4 * q], old[q].y + res[4 * q + 1], old[q].z + res[4 * q + 2],
+                                  old[q].w + res[4 * q + 3]);
+          } else if (row_in) {
 #pragma unroll
-              for (int q = 0; q < 32; ++q)
-                if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
-            }
+            for (int q = 0; q < 32; ++q)
+              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
           }
         }
       }
@@ -476,13 +490,14 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     dev::set_status(a.status, kStatusTimeout);
   }
   __syncthreads();
-  if (mma_warp && lane == 0 && s_abort) {
-    // wait (bounded) for MMAs and copies still in flight before releasing
-    // TMEM and shared memory; phases already complete return at once
-    if (g_committed > 0) {
-      const int64_t gl = g_committed - 1;
-      dev::mbar_wait_bounded(&bar_mma[gl % kSepBStages], (uint32_t)((gl / kSepBStages) & 1), 1LL << 28);
-    }
+  // on abort, wait (bounded) for MMAs and copies still in flight before
+  // releasing TMEM and shared memory; phases already complete return at once
+  if (mma_warp && lane == 0 && s_abort && g_committed > 0) {
+    const int64_t gl = g_committed - 1;
+    dev::mbar_wait_bounded(&bar_mma[gl % kSepBStages], (uint32_t)((gl / kSepBStages) & 1), 1LL << 28);
+    dev::mbar_wait_bounded(&bar_aempty[gl % kSepAStages], (uint32_t)((gl / kSepAStages) & 1), 1LL << 28);
+  }
+  if (copy_warp && lane == 0 && s_abort) {
     for (int64_t s = a_issued > kSepAStages ? a_issued - kSepAStages : 0; s < a_issued; ++s)
       dev::mbar_wait_bounded(&bar_full[s % kSepAStages], (uint32_t)((s / kSepAStages) & 1), 1LL << 28);
     for (int64_t s = t_issued > kSepTStages ? t_issued - kSepTStages : 0; s < t_issued; ++s)
