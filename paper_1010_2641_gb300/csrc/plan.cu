@@ -231,6 +231,7 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.ztab);
   release(d.sep_A);
   release(d.sep_partial);
+  release(d.sep_chunks);
   release(d.sep_axis_s);
   release(d.sep_axis64);
   release(d.sep_virt);

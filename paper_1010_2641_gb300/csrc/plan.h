@@ -111,7 +111,8 @@ struct DeviceBuffers {
   float4* ztab = nullptr;           // [n_afb][n_slots][32] Z1, Z2 per call
   // separable path
   void* sep_A = nullptr;            // A operand blocks (f16 hi/lo)
-  float* sep_partial = nullptr;     // [split][2][sep_ns] planar
+  float* sep_partial = nullptr;     // [chunk][2][sep_ns] planar
+  Segment* sep_chunks = nullptr;    // separable atom chunks: one species each, step-aligned slots
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
   double* sep_axis64 = nullptr;     // separable grid axes, full S
   float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid
@@ -169,6 +170,7 @@ struct scatter_plan_s {
   int64_t sep_mt = 0, sep_nt = 0, sep_steps = 0;
   int64_t sep_n[3] = {0, 0, 0};                  // separable grid shape (GID: n_h, n_k, 4 n_af)
   int64_t sep_ns = 0;
+  int32_t sep_n_chunks = 0;
   std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
   bool adj_ready = false;
   int adj_split = 1;

@@ -33,10 +33,12 @@
 // computing B from the atom records, instead of loading tabulated factors
 // through L1, keeps the rest of the shared-memory traffic to the A copies
 // and the B stores.
-// Every 256 steps and at every species boundary the accumulator is read
-// from TMEM (tcgen05.ld), multiplied by f_s(|S|) and added into planar FP32
-// partials owned by the CTA; k_sep_reduce sums the chunks in order and
-// applies the translation phase.
+// Atom chunks (grid y) hold one species each.  Every 256 steps and at the
+// end of the chunk the accumulator is read from TMEM (tcgen05.ld) and added
+// into planar FP32 partials owned by the CTA (shorter groups keep the
+// tensor core's FP32 accumulation error down); k_sep_reduce sums the chunks
+// in order, each times its species' f_s(|S|), and applies the translation
+// phase.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <algorithm>
@@ -177,30 +179,21 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
 
 struct SepArgs {
   const uint4* A;
-  const float4* atom4;  // per slot (x', y', z', c)
-  const Segment* segs;
-  const int32_t* chunk_seg_off;
-  const float* coef;
+  const float4* atom4;    // per slot (x', y', z', c)
+  const Segment* chunks;  // per blockIdx.y: one species, slots a multiple of 16
   const float* axis_s;
   int64_t n0, n1, n2, n_s;
   int64_t n_slots, n_steps, n_mt, n_nt;
-  float H[3];
-  float inv4a2;
-  float* partial;   // [chunk][2][n_s] planar (re plane, im plane)
+  float* partial;   // [chunk][2][n_s] planar (re plane, im plane), T without f_s
   unsigned* status;
 };
 
 // Accumulation groups: the steps between two TMEM flushes (every kSepFlush
-// steps and at every species boundary).  Both roles walk them identically.
+// steps and at the end of the chunk).  Both roles walk them identically.
 struct SepGroups {
-  int cur_seg, seg_hi;
-  int64_t seg_end_ks, grp_start;
-  __device__ bool ends_at(int64_t ks) const { return ks + 1 == seg_end_ks || ks + 1 - grp_start >= kSepFlush; }
-  __device__ void advance(int64_t ks, const Segment* segs) {  // past the group ending at ks
-    const bool seg_done = ks + 1 == seg_end_ks;
-    grp_start = ks + 1;
-    if (seg_done && ++cur_seg < seg_hi) seg_end_ks = segs[cur_seg].end / kSepStep;
-  }
+  int64_t ks_end, grp_start;
+  __device__ bool ends_at(int64_t ks) const { return ks + 1 == ks_end || ks + 1 - grp_start >= kSepFlush; }
+  __device__ void advance(int64_t ks) { grp_start = ks + 1; }
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -269,11 +262,9 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
-  // the chunk's steps are contiguous; species boundaries fall on step edges
-  const int64_t ks_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin / kSepStep : 0;
-  const int64_t ks_end = seg_lo < seg_hi ? a.segs[seg_hi - 1].end / kSepStep : 0;
-  SepGroups grp{seg_lo, seg_hi, seg_lo < seg_hi ? a.segs[seg_lo].end / kSepStep : 0, ks_begin};
+  // the chunk's steps: one species, slot bounds on step edges
+  const int64_t ks_begin = a.chunks[chunk].begin / kSepStep, ks_end = a.chunks[chunk].end / kSepStep;
+  SepGroups grp{ks_end, ks_begin};
   bool ok = true;
   // copies issued and MMA steps committed (steps), for the drain on abort
   int64_t a_issued = 0, t_issued = 0, g_committed = 0;
@@ -351,7 +342,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         mma_commit(&bar_aempty[ast]);
         g_committed = g + 1;
         if (grp.ends_at(ks)) {
-          grp.advance(ks, a.segs);
+          grp.advance(ks);
           ++flushes;
         }
       }
@@ -407,7 +398,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       }
       if (!grp.ends_at(ks)) continue;
 
-      // ---- group end: TMEM -> f_s(|S|) x T -> planar partials ---------------
+      // ---- group end: TMEM -> planar partials --------------------------------
       // the commit of step g covers every earlier MMA of the group
       w = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)((g / kSepBStages) & 1));
       if (!__all_sync(0xffffffffu, w)) {
@@ -415,53 +406,37 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         break;
       }
       tc_fence_after();
-      const float* cf = a.coef + kNCoef * a.segs[grp.cur_seg].species;
+      // TMEM lane = A row 2a + ri: this thread's row is Re T (ri = 0) or Im T
+      // (ri = 1) of point a, i.e. one plane of the partials
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;  // A row = 2a + ri
+        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
         const int64_t pa = m_row >> 1;
-        const bool is_im = (m_row & 1) != 0;
-        const float Sx = a.H[0] + (pa < a.n0 ? a.axis_s[pa] : 0.f);
+        float* plane = (m_row & 1) ? part_im : part_re;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
           const int64_t bc0 = nt * kSepN + col0 + cc;
-          float* dst = (is_im ? part_im : part_re) + pa * nbc + bc0;
+          float* dst = plane + pa * nbc + bc0;
           const bool row_in = pa < a.n0 && bc0 < nbc;
           const bool vec = row_in && bc0 + 32 <= nbc && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
-          // the partials' loads go out before the TMEM read and the form factors
+          // the partials' loads go out before the TMEM read
           float4 old[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             old[q] = (vec && !first_flush) ? reinterpret_cast<const float4*>(dst)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
-          int64_t ib = bc0 / a.n2, ic = bc0 % a.n2;
-          float res[32];
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const float other = __shfl_xor_sync(0xffffffffu, v[q], 1);
-            const float re = is_im ? other : v[q], im = is_im ? v[q] : other;
-            const int64_t jb = ib < a.n1 ? ib : a.n1 - 1;
-            const float Sy = a.H[1] + a.axis_s[a.n0 + jb], Sz = a.H[2] + a.axis_s[a.n0 + a.n1 + ic];
-            const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
-            const float2 F = dev::form_factor(cf, s2);
-            res[q] = is_im ? fmaf(F.x, im, F.y * re) : fmaf(F.x, re, -F.y * im);
-            if (++ic == a.n2) {
-              ic = 0;
-              ++ib;
-            }
-          }
           if (vec) {
             float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              d4[q] = make_float4(old[q].x + res[4 * q], old[q].y + res[4 * q + 1], old[q].z + res[4 * q + 2],
-                                  old[q].w + res[4 * q + 3]);
+              d4[q] = make_float4(old[q].x + v[4 * q], old[q].y + v[4 * q + 1], old[q].z + v[4 * q + 2],
+                                  old[q].w + v[4 * q + 3]);
           } else if (row_in) {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + res[q];
+              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + v[q];
           }
         }
       }
@@ -469,7 +444,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_tfree);
-      grp.advance(ks, a.segs);
+      grp.advance(ks);
     }
     if (ok && first_flush) {
       // empty chunk: its partials are zero
@@ -508,21 +483,31 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSepTmemCols));
 }
 
-// Sum of the planar chunk partials in order, translation phase, outputs.
-__global__ void k_sep_reduce(const float* __restrict__ partial, int split, int64_t n_s, const double* __restrict__ axis64,
-                             int64_t n0, int64_t n1, int64_t n2, double H0, double H1, double H2,
-                             const double* __restrict__ shift, float2* out_amp, float* out_int) {
+// Sum over the chunks in order of f_s(|S|) x T_chunk (Eq. 2: each chunk holds
+// one species s), translation phase, outputs.
+__global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* __restrict__ chunks, int n_chunks,
+                             const float* __restrict__ coef, float inv4a2, int64_t n_s,
+                             const double* __restrict__ axis64, int64_t n0, int64_t n1, int64_t n2, double H0,
+                             double H1, double H2, const double* __restrict__ shift, float2* out_amp, float* out_int) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_s) return;
-  float2 v = make_float2(0.f, 0.f);
-  for (int c = 0; c < split; ++c) {
-    v.x += partial[(int64_t)c * 2 * n_s + m];
-    v.y += partial[(int64_t)c * 2 * n_s + n_s + m];
+  const int64_t i2 = m % n2, line = m / n2, i1 = line % n1, i0 = line / n1;
+  const double S0 = axis64[i0], S1 = axis64[n0 + i1], S2 = axis64[n0 + n1 + i2];
+  const float s2 = (float)(S0 * S0 + S1 * S1 + S2 * S2) * inv4a2;
+  float2 v = make_float2(0.f, 0.f), F = make_float2(0.f, 0.f);
+  int cur = -1;
+  for (int c = 0; c < n_chunks; ++c) {
+    const int sp = chunks[c].species;
+    if (sp != cur) {
+      F = dev::form_factor(coef + kNCoef * sp, s2);
+      cur = sp;
+    }
+    const float re = partial[(int64_t)c * 2 * n_s + m], im = partial[(int64_t)c * 2 * n_s + n_s + m];
+    v.x += F.x * re - F.y * im;
+    v.y += F.x * im + F.y * re;
   }
-  if (shift[0] != 0.0 || shift[1] != 0.0 || shift[2] != 0.0) {
-    const int64_t i2 = m % n2, line = m / n2, i1 = line % n1, i0 = line / n1;
-    v = dev::cmul(dev::shift_phase(axis64[i0] - H0, axis64[n0 + i1] - H1, axis64[n0 + n1 + i2] - H2, shift), v);
-  }
+  if (shift[0] != 0.0 || shift[1] != 0.0 || shift[2] != 0.0)
+    v = dev::cmul(dev::shift_phase(S0 - H0, S1 - H1, S2 - H2, shift), v);
   if (out_amp) out_amp[m] = v;
   if (out_int) out_int[m] = v.x * v.x + v.y * v.y;
 }
@@ -608,10 +593,29 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   p->sep_steps = n_steps;
   cudaError_t e;
   const size_t a_bytes = (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
-  const size_t part_bytes = (size_t)split * 2 * (size_t)p->sep_ns * sizeof(float);
+  // atom chunks: every species segment split into step-aligned pieces, about
+  // `split` pieces in all, so that each chunk carries a single form factor
+  std::vector<Segment> chunks;
+  int64_t total_steps = 0;
+  for (const Segment& sg : p->all_segs)
+    if (sg.instance == 0 && sg.end > sg.begin) total_steps += (sg.end - sg.begin) / kSepStep;
+  for (const Segment& sg : p->all_segs) {
+    if (sg.instance != 0 || sg.end <= sg.begin) continue;
+    const int64_t steps = (sg.end - sg.begin) / kSepStep;
+    const int64_t k = std::max<int64_t>(1, std::llround((double)split * (double)steps / (double)total_steps));
+    const int64_t per = (steps + k - 1) / k;
+    for (int64_t b = 0; b < steps; b += per)
+      chunks.push_back(Segment{sg.begin + b * kSepStep, sg.begin + std::min(steps, b + per) * kSepStep, sg.species, 0});
+  }
+  if (chunks.empty()) chunks.push_back(Segment{0, 0, 0, 0});  // no atoms: one empty chunk, zero partials
+  p->sep_n_chunks = (int32_t)chunks.size();
+  const size_t part_bytes = (size_t)p->sep_n_chunks * 2 * (size_t)p->sep_ns * sizeof(float);
+  const size_t chunk_bytes = chunks.size() * sizeof(Segment);
   if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
   if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc separable partials");
+  if ((e = cudaMalloc(&p->d.sep_chunks, chunk_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc chunks");
+  cudaMemcpy(p->d.sep_chunks, chunks.data(), chunk_bytes, cudaMemcpyHostToDevice);
   if ((e = cudaMalloc(&p->d.sep_axis_s, alls.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
   if ((e = cudaMalloc(&p->d.sep_axis64, all64.size() * sizeof(double))) != cudaSuccess) return cuda_status(e, "axes");
   cudaMemcpy(p->d.sep_axis_s, alls.data(), alls.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -621,7 +625,7 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     virt_bytes = (size_t)p->sep_ns * sizeof(float2);
     if ((e = cudaMalloc(&p->d.sep_virt, virt_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc virtual map");
   }
-  p->base_bytes += (int64_t)(a_bytes + part_bytes + virt_bytes);
+  p->base_bytes += (int64_t)(a_bytes + part_bytes + chunk_bytes + virt_bytes);
   static_assert(kSepSmem + 4096 <= 227 * 1024, "dynamic + static shared memory of k_sep");
   if ((e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem)) != cudaSuccess)
     return cuda_status(e, "separable shared memory attribute");
@@ -640,7 +644,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   t.n_steps = p->sep_steps;
   t.n_mt = p->sep_mt;
   t.A = static_cast<uint4*>(p->d.sep_A);
-  const int n_chunks = (int)p->chunk_seg_off.size() - 1;
+  const int n_chunks = p->sep_n_chunks;
   if (p->n_slots > 0) {
     const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;  // real tiles; a padding tile is never read
     k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
@@ -649,9 +653,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   SepArgs a{};
   a.A = static_cast<const uint4*>(p->d.sep_A);
   a.atom4 = p->d.atom4;
-  a.segs = p->d.segs;
-  a.chunk_seg_off = p->d.chunk_seg_off;
-  a.coef = p->d.coef;
+  a.chunks = p->d.sep_chunks;
   a.axis_s = p->d.sep_axis_s;
   a.n0 = p->sep_n[0];
   a.n1 = p->sep_n[1];
@@ -661,18 +663,17 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.n_steps = p->sep_steps;
   a.n_mt = p->sep_mt;
   a.n_nt = p->sep_nt;
-  for (int d = 0; d < 3; ++d) a.H[d] = (float)p->inst[0].H[d];
-  a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.partial = p->d.sep_partial;
   a.status = p->d.status;
-  dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)std::max(n_chunks, 1));
+  dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)n_chunks);
   timing_begin(p, st);
   k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
   timing_end(p, st);
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
-      p->d.sep_partial, std::max(n_chunks, 1), p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
+      p->d.sep_partial, p->d.sep_chunks, n_chunks, p->d.coef, (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
+      p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
       p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, gid ? p->d.sep_virt : amp_out,
       gid ? nullptr : int_out);
   p->last_launches += 1;
