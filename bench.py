@@ -135,22 +135,28 @@ def measured_peak(key: str, fallback: float):
         return fallback, f"fallback {fallback} (of fallback)"
 
 
-def kernel_source_hash() -> str:
+GENERIC_SOURCES = ("forward.cu", "generic_impl.cuh", "device_common.cuh", "plan.h")
+
+
+def kernel_source_hash(files=GENERIC_SOURCES) -> str:
     h = hashlib.sha1()
-    for f in ("forward.cu", "device_common.cuh", "plan.h"):
+    for f in files:
         h.update((ROOT / "paper_1010_2641_gb300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:12]
 
 
-def profiled_traffic():
-    """dram bytes per launch of the generic kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = ROOT / "profiles" / "generic_strained_sphere.md"
+SEP_SOURCES = ("separable.cu", "device_common.cuh", "plan.h")
+
+
+def profiled_traffic(name="generic_strained_sphere.md", files=GENERIC_SOURCES):
+    """dram bytes per launch of a kernel from its committed ncu summary, if
+    the summary was taken on the current kernel source."""
+    p = ROOT / "profiles" / name
     if not p.exists():
         return None
     text = p.read_text()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(source sha1 ([0-9a-f]+)\)", text)
-    if not m or m.group(2) != kernel_source_hash():
+    if not m or m.group(2) != kernel_source_hash(files):
         return None
     return float(m.group(1))
 
@@ -296,7 +302,8 @@ def run_gpu(args, rank, world, local_rank):
         peak, basis = measured_peak("bf16_tflops", 1900.0)
         achieved = executed / (t_kern * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)",
+                "traffic": None if args.grid else profiled_traffic("separable_strained_sphere.md", SEP_SOURCES),
+                "kernel": "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)",
                 "kernel_ms": t_kern, "useful_tflops": useful / (t_kern * 1e-3) / 1e12,
                 "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
     elif sm_mhz:

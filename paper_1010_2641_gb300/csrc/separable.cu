@@ -205,20 +205,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // warp 9 (one lane) issues the TMA copies.  Hand-offs go through mbarriers
 // only:
 //   bar_full[a]   A block of a step arrived            (TMA, 1 arrival + bytes)
-//   bar_aempty[a] MMAs that read the A stage done      (commit)
+//   bar_done[a]   MMAs of the step done (one commit per step); frees the A
+//                 stage of that step and the B stage it read
 //   bar_atom[t]   atom records of a step arrived       (TMA)
 //   bar_tempty[t] atom records read by the formation   (8 warps)
 //   bar_bfull[b]  B block of a step formed             (8 warps)
-//   bar_mma[b]    MMAs of the step done (commit); frees its B stage
 //   bar_tfree     accumulators read out after a group end (8 warps)
 __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
+  // a B stage is freed by the done barrier of the step that read it: the A
+  // ring (and with it the done ring) must be at least as deep as the B ring
+  static_assert(kSepBStages <= kSepAStages, "B-stage reuse is tracked on the done ring");
   extern __shared__ __align__(1024) unsigned char sep_smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[kSepAStages];
-  __shared__ __align__(8) uint64_t bar_aempty[kSepAStages];
+  __shared__ __align__(8) uint64_t bar_done[kSepAStages];
   __shared__ __align__(8) uint64_t bar_atom[kSepTStages];
   __shared__ __align__(8) uint64_t bar_tempty[kSepTStages];
   __shared__ __align__(8) uint64_t bar_bfull[kSepBStages];
-  __shared__ __align__(8) uint64_t bar_mma[kSepBStages];
   __shared__ __align__(8) uint64_t bar_tfree;
   __shared__ __align__(16) float4 ring_atom[kSepTStages][kSepStep];
   __shared__ uint32_t tmem_slot;
@@ -243,7 +245,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   if (tid == 0) {
     for (int s = 0; s < kSepAStages; ++s) {
       dev::mbar_init(&bar_full[s], 1);
-      dev::mbar_init(&bar_aempty[s], 1);
+      dev::mbar_init(&bar_done[s], 1);
     }
     for (int s = 0; s < kSepTStages; ++s) {
       dev::mbar_init(&bar_atom[s], 1);
@@ -251,7 +253,6 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     }
     for (int s = 0; s < kSepBStages; ++s) {
       dev::mbar_init(&bar_bfull[s], kSepFormWarps);
-      dev::mbar_init(&bar_mma[s], 1);
     }
     dev::mbar_init(&bar_tfree, kSepFormWarps);
     s_abort = 0;
@@ -291,7 +292,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         dev::bulk_g2s(&ring_atom[tst][0], a.atom4 + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
         t_issued = g + 1;
         if (g >= kSepAStages &&
-            !dev::mbar_wait_bounded(&bar_aempty[ast], (uint32_t)(((g - kSepAStages) / kSepAStages) & 1))) {
+            !dev::mbar_wait_bounded(&bar_done[ast], (uint32_t)(((g - kSepAStages) / kSepAStages) & 1))) {
           ok = false;
           break;
         }
@@ -306,7 +307,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       int64_t flushes = 0;  // groups read out before the current one
       int64_t g = 0;
       for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
-        if (s_abort) {
+        if ((g & 15) == 0 && s_abort) {  // waits are bounded; a prompt exit is a bonus
           ok = false;
           break;
         }
@@ -338,8 +339,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
             mma_f16(d, a_lo, b_hi, 1u);
           }
         }
-        mma_commit(&bar_mma[bst]);
-        mma_commit(&bar_aempty[ast]);
+        mma_commit(&bar_done[ast]);
         g_committed = g + 1;
         if (grp.ends_at(ks)) {
           grp.advance(ks);
@@ -365,7 +365,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       // every lane waits, the warp agrees on the outcome
       bool w = !s_abort;
       if (w && g >= kSepBStages)
-        w = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)(((g - kSepBStages) / kSepBStages) & 1));
+        w = dev::mbar_wait_bounded(&bar_done[(g - kSepBStages) % kSepAStages],
+                                   (uint32_t)(((g - kSepBStages) / kSepAStages) & 1));
       if (w) w = dev::mbar_wait_bounded(&bar_atom[tst], (uint32_t)((g / kSepTStages) & 1));
       if (!__all_sync(0xffffffffu, w)) {
         ok = false;
@@ -400,7 +401,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 
       // ---- group end: TMEM -> planar partials --------------------------------
       // the commit of step g covers every earlier MMA of the group
-      w = dev::mbar_wait_bounded(&bar_mma[bst], (uint32_t)((g / kSepBStages) & 1));
+      w = dev::mbar_wait_bounded(&bar_done[g % kSepAStages], (uint32_t)((g / kSepAStages) & 1));
       if (!__all_sync(0xffffffffu, w)) {
         ok = false;
         break;
@@ -469,8 +470,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   // releasing TMEM and shared memory; phases already complete return at once
   if (mma_warp && lane == 0 && s_abort && g_committed > 0) {
     const int64_t gl = g_committed - 1;
-    dev::mbar_wait_bounded(&bar_mma[gl % kSepBStages], (uint32_t)((gl / kSepBStages) & 1), 1LL << 28);
-    dev::mbar_wait_bounded(&bar_aempty[gl % kSepAStages], (uint32_t)((gl / kSepAStages) & 1), 1LL << 28);
+    dev::mbar_wait_bounded(&bar_done[gl % kSepAStages], (uint32_t)((gl / kSepAStages) & 1), 1LL << 28);
   }
   if (copy_warp && lane == 0 && s_abort) {
     for (int64_t s = a_issued > kSepAStages ? a_issued - kSepAStages : 0; s < a_issued; ++s)
