@@ -65,6 +65,21 @@ def workload_name():
             "S grid around (004), step 0.002 r.l.u.")
 
 
+def host_cpu() -> str:
+    """Machine and CPU model of the host (best effort, for the report)."""
+    import platform
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu part"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model} x{os.cpu_count()}".strip()
+
+
 def sample_indices(n_s: int, n: int, seed: int = 7):
     return np.sort(np.random.default_rng(seed).choice(n_s, n, replace=False))
 
@@ -337,9 +352,20 @@ def run_gpu(args, rank, world, local_rank):
         ref = oracle_step(c, S)
         dt = time.perf_counter() - t0
         got = A.cpu().numpy()[idx].astype(np.complex128)
-        out["cpu_baseline"] = {"value": n_atoms * len(idx) / dt, "unit": UNIT, "cores": oracle.num_threads(),
+        cores = oracle.num_threads()
+        # single-thread rate on a smaller sample (compare: the paper's 122e6 pairs/s/core, SSE FP32)
+        idx1 = idx[: max(1, len(idx) // 32)]
+        oracle.set_threads(1)
+        t1 = time.perf_counter()
+        oracle_step(c, W.grid_points(axes)[idx1])
+        dt1 = time.perf_counter() - t1
+        oracle.set_threads(0)
+        out["cpu_baseline"] = {"value": n_atoms * len(idx) / dt, "unit": UNIT, "cores": cores,
                                "kind": "oracle",
-                               "sample": f"{len(idx)} of {n_s} grid points (seeded), all {n_atoms} atoms, {dt:.1f} s"}
+                               "sample": f"{len(idx)} of {n_s} grid points (seeded), all {n_atoms} atoms, {dt:.1f} s",
+                               "per_core": n_atoms * len(idx) / dt / cores,
+                               "single_thread": n_atoms * len(idx1) / dt1,
+                               "host": host_cpu()}
         out["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                            "points": int(len(idx)), "tolerance": 1e-4}
     if not args.no_paths and rank == 0 and world == 1:
@@ -361,9 +387,32 @@ def _time_calls(fn, plan, reps=2):
     return float(np.mean(ms))
 
 
+def _rate_roof(units, ms, per_sm_clk, n_sm, clk, unit, bound, basis):
+    """Roofline object of a compute-bound row: `units` of work in `ms`
+    against per_sm_clk units per SM per clock at the sampled SM clock."""
+    if not (clk and clk.get("sm_mhz")):
+        return None
+    peak = n_sm * per_sm_clk * clk["sm_mhz"] * 1e6
+    achieved = units / (ms * 1e-3)
+    return {"bound": bound, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": unit, "frac": achieved / peak,
+            "peak_basis": f"{n_sm} SMs x {per_sm_clk:g} {basis}/SM/clk x {clk['sm_mhz']:.0f} MHz (median sampled)"}
+
+
+def _tensor_roof(n0, n12, n_atoms_padded, ms):
+    """Executed-flop roofline of k_sep on an n0 x n12 separable grid."""
+    m_pad = -(-2 * n0 // 128) * 128
+    n_pad = -(-n12 // 256) * 256
+    executed = 6.0 * m_pad * n_pad * 2 * n_atoms_padded
+    peak, basis = measured_peak("bf16_tflops", 1900.0)
+    achieved = executed / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+
+
 def measure_paths(args, dev, clk):
     """The other rows of the hot path, each on its own workload (device time
-    of the row's main kernel, CUDA events on the launching stream)."""
+    of the row's main kernel, CUDA events on the launching stream), each with
+    the roofline of its binding unit."""
     import torch
     from paper_1010_2641_gb300 import api
     from paper_1010_2641_gb300 import workloads as W
@@ -376,10 +425,12 @@ def measure_paths(args, dev, clk):
     plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, path=other, timing=True)
     ms = _time_calls(lambda: plan.amplitude(xyz), plan)
     row = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "workload": "strained sphere, full map"}
-    if other == "generic" and clk and clk.get("sm_mhz"):
-        peak = plan.info()["n_sm"] * 8.0 * clk["sm_mhz"] * 1e6
-        row["roofline"] = {"bound": "alu", "achieved": n_atoms * n_s / (ms * 1e-3) / 1e9, "peak": peak / 1e9,
-                           "unit": "Gpair/s", "frac": n_atoms * n_s / (ms * 1e-3) / peak}
+    n_sm = plan.info()["n_sm"]
+    if other == "generic":
+        row["roofline"] = _rate_roof(n_atoms * n_s, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+                                     "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")
+    else:
+        row["roofline"] = _tensor_roof(GRID[0], GRID[1] * GRID[2], plan.info()["n_atoms_padded"], ms)
     res[f"{other}_sphere"] = row
     del plan
     # plain FP64 kernel on a 1/16 slice of the same map (every 16th l plane)
@@ -400,7 +451,10 @@ def measure_paths(args, dev, clk):
     ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
     ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
     res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
-                           "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr"}
+                           "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr",
+                           "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms,
+                                                  MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk, "Gpair/s",
+                                                  "alu", "pairs (2 MUFU sin/cos each)")}
     del plan, x, A, I_obs
     # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
     isl = W.truncated_pyramid()
@@ -411,14 +465,18 @@ def measure_paths(args, dev, clk):
     ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
     m_gid = 512 * 512 * 32
     res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
-                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel"}
+                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel",
+                          # 16 FFMA per (atom, point) for the four beams: 8 points = 32 beam-pairs per SM per clock
+                          "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 32.0, n_sm, clk, "Gbeam-pair/s",
+                                                 "alu", "beam-pairs (16 FFMA per atom-point, 128 FFMA/SM/clk)")}
     del plan
     plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
                     gid=gid, path="separable", timing=True)
     ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
     res["dwba_island_separable"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
                                     "kernel_ms": ms,
-                                    "workload": "same map, beams stacked on a virtual l axis, tensor cores"}
+                                    "workload": "same map, beams stacked on a virtual l axis, tensor cores",
+                                    "roofline": _tensor_roof(512, 512 * 4 * 32, plan.info()["n_atoms_padded"], ms)}
     del plan, x
     # batched persistent launch, CUDA-graph replay (64 uneven crystals)
     bx, bs, bcoef, bS, ao, so = W.ewald_batch()
@@ -428,8 +486,54 @@ def measure_paths(args, dev, clk):
     ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
     pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
     res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
-                          "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each"}
+                          "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
+                          "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+                                                 "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
     return res
+
+
+def run_sweep(args):
+    """The paper's speed test (Section 3, its speed figure): random atoms in a
+    100^3 box, random S within +-0.5 of (004), occupancy 1, f = 1; pairs/s of
+    the generic kernel for every (atoms, reflections) in {1e2 .. 1e6}^2, each
+    spot-checked against the oracle.  Prints one JSON object."""
+    import torch
+    import oracle
+    from paper_1010_2641_gb300 import api
+    from paper_1010_2641_gb300 import workloads as W
+    oracle.build()
+    dev = "cuda:0"
+    torch.cuda.set_device(0)
+    sizes = [int(v) for v in args.sweep.split(",")]
+    unit = W.unit_species()
+    rows = []
+    for n_atoms in sizes:
+        for n_s in sizes:
+            xyz, S = W.random_sweep(n_atoms, n_s, seed=1000 * len(str(n_atoms)) + len(str(n_s)))
+            plan = api.Plan(unit, W.LATTICE_A, n_atoms, s_list=S, path="generic", timing=True,
+                            autotune=args.autotune)
+            x = torch.tensor(xyz, dtype=torch.float64, device=dev)
+            out = torch.empty(n_s, dtype=torch.complex64, device=dev)
+            ms = _time_calls(lambda: plan.amplitude(x, out=out), plan, reps=5 if n_atoms * n_s < 1e11 else 2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.amplitude(x, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            call_ms = e0.elapsed_time(e1)
+            idx = sample_indices(n_s, min(n_s, 16), seed=3)
+            ref = oracle.amplitude(xyz, S[idx], unit, W.LATTICE_A)
+            got = out.cpu().numpy()[idx].astype(np.complex128)
+            err = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+            info = plan.info()
+            rows.append({"atoms": n_atoms, "reflections": n_s, "value": n_atoms * n_s / (ms * 1e-3),
+                         "kernel_ms": ms, "call_ms": call_ms, "rel_l2_16pts": err, "threads": info["threads"],
+                         "points_per_thread": info["points_per_thread"], "split_k": info["split_k"],
+                         "atoms_per_thread": info["atoms_per_thread"]})
+            del plan, x, out
+    print(json.dumps({"sweep": "generic kernel, random atoms x random reflections (paper's speed test)",
+                      "unit": UNIT, "rows": rows}))
+    return 0
 
 
 def main():
@@ -444,6 +548,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-paths", action="store_true", help="skip the other rows' measurements")
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
+    ap.add_argument("--sweep", default=None, help="speed sweep over atoms x reflections, e.g. 100,1000,10000")
     ap.add_argument("--path", default="separable", choices=["generic", "separable"],
                     help="kernel family of the headline line (both meet the 1e-4 tolerance on this map)")
     args = ap.parse_args()
@@ -455,6 +560,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

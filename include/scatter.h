@@ -148,6 +148,11 @@ typedef struct scatter_options {
                                 -1 = off)                                     */
   int32_t timing;            /* 1: record CUDA events around the main kernel
                                 of every call (see scatter_plan_timing)       */
+  int32_t atoms_per_thread;  /* generic path, one instance: 1, 2, 4, 8 or 16
+                                selects the atom-parallel form (threads share
+                                the reflections and split the atoms, Section 3)
+                                with that many atoms per thread; 0 = chosen by
+                                the heuristic / autotuner; -1 = never         */
 } scatter_options;
 
 typedef struct scatter_plan_s* scatter_plan_t;
@@ -164,6 +169,7 @@ typedef struct scatter_plan_info {
   int64_t workspace_bytes;   /* device memory owned by the plan                */
   double center_hkl[3];      /* H of instance 0                                */
   double shift[3];           /* integer centring vector t of instance 0        */
+  int32_t atoms_per_thread;  /* > 0: the atom-parallel form was chosen        */
 } scatter_plan_info;
 
 /* ------------------------------------------------------------------------ */

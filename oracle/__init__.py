@@ -62,6 +62,8 @@ def _load():
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
         lib.oracle_fd_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, i64, P, f64, P]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -90,6 +92,11 @@ def _atoms(xyz, species, occ, coef):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Thread count of later oracle calls (n < 1: the OpenMP default)."""
+    _load().oracle_set_threads(int(n))
 
 
 def form_factor(coef, q_inv_angstrom: float) -> complex:

@@ -286,6 +286,18 @@ void oracle_fd_grad(int64_t n_atoms, const double* xyz, const int32_t* species,
   free(A);
 }
 
+/* Threads of the following calls (timing the oracle on one core); n < 1
+ * restores the runtime default.  Host control only: no effect on results. */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  static int default_n = 0;
+  if (default_n == 0) default_n = omp_get_max_threads();
+  omp_set_num_threads(n >= 1 ? n : default_n);
+#else
+  (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the oracle runs with (for reporting). */
 int oracle_num_threads(void) {
   int n = 1;

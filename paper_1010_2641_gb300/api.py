@@ -53,13 +53,16 @@ class Plan:
     center : reference reflection H (integers) or None (automatic).
     gid : dict(wavelength=, alpha_i=, delta=, beta=) for grazing incidence.
     atom_off, s_off : batch CSR offsets (lists only).
+    atoms_per_thread : generic path, one instance: 1/2/4/8/16 forces the
+        atom-parallel form (for many atoms and few reflections), 0 lets the
+        heuristic or autotuner choose, -1 keeps the S-parallel kernel.
     """
 
     def __init__(self, coef, lattice_a: float, n_atoms: int, *, s_list=None, axes: Sequence | None = None,
                  atom_species=None, center=None, path: str = "auto", gid: dict | None = None,
                  atom_off=None, s_off=None, autotune: bool = False, tune_cache: str | None = None,
                  threads: int = 0, points_per_thread: int = 0, split_k: int = 0, use_graph: bool = True,
-                 timing: bool = False):
+                 timing: bool = False, atoms_per_thread: int = 0):
         L = B.lib()
         self._keep = []
         pr = B.scatter_problem()
@@ -119,6 +122,7 @@ class Plan:
         op.threads, op.points_per_thread, op.split_k = threads, points_per_thread, split_k
         op.use_graph = 0 if use_graph else -1
         op.timing = int(bool(timing))
+        op.atoms_per_thread = int(atoms_per_thread)
         h = ctypes.c_void_p()
         B.check(L.scatter_plan(ctypes.byref(pr), ctypes.byref(op), ctypes.byref(h)), "scatter_plan")
         self._h = h

@@ -70,13 +70,14 @@ class scatter_problem(ctypes.Structure):
 
 class scatter_options(ctypes.Structure):
     _fields_ = [("path", c_int32), ("autotune", c_int32), ("tune_cache", c_char_p), ("threads", c_int32),
-                ("points_per_thread", c_int32), ("split_k", c_int32), ("use_graph", c_int32), ("timing", c_int32)]
+                ("points_per_thread", c_int32), ("split_k", c_int32), ("use_graph", c_int32), ("timing", c_int32),
+                ("atoms_per_thread", c_int32)]
 
 
 class scatter_plan_info(ctypes.Structure):
     _fields_ = [("path", c_int32), ("threads", c_int32), ("points_per_thread", c_int32), ("split_k", c_int32),
                 ("n_sm", c_int32), ("n_atoms_padded", c_int64), ("n_s", c_int64), ("workspace_bytes", c_int64),
-                ("center_hkl", c_double * 3), ("shift", c_double * 3)]
+                ("center_hkl", c_double * 3), ("shift", c_double * 3), ("atoms_per_thread", c_int32)]
 
 
 class scatter_microbench_result(ctypes.Structure):

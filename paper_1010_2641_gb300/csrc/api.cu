@@ -177,6 +177,7 @@ extern "C" scatter_status scatter_plan_get_info(scatter_plan_t p, scatter_plan_i
   info->threads = p->tiling.threads;
   info->points_per_thread = p->tiling.R;
   info->split_k = p->tiling.split_k;
+  info->atoms_per_thread = p->tiling.atom_k;
   info->n_sm = p->n_sm;
   info->n_atoms_padded = p->n_slots;
   info->n_s = p->n_s;

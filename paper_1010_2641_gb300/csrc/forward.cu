@@ -361,7 +361,22 @@ scatter_status launch_prep(scatter_plan_t p, const double* xyz, const float* occ
   return cuda_status(cudaGetLastError(), "prep launch");
 }
 
+scatter_status launch_generic_reduce(scatter_plan_t p, int n_chunks, float2* amp_out, float* int_out,
+                                     cudaStream_t st) {
+  GenericArgs a = make_args(p);
+  a.partial = p->d.partial;
+  a.out_amp = amp_out;
+  a.out_int = int_out;
+  const int64_t nb = (p->n_s + 255) / 256;
+  if (nb > 0) {
+    k_reduce<<<(unsigned)nb, 256, 0, st>>>(a, n_chunks, mode_of(p) == kModeGrid);
+    p->last_launches += 1;
+  }
+  return cuda_status(cudaGetLastError(), "generic reduction launch");
+}
+
 scatter_status launch_generic(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st) {
+  if (p->tiling.atom_k > 0) return launch_atompar(p, amp_out, int_out, st);
   const Tiling& t = p->tiling;
   void* fn = pick_generic(mode_of(p), t.R, t.threads);
   if (!fn) return fail(SCATTER_ERR_UNSUPPORTED, "no generic kernel for R=%d threads=%d", t.R, t.threads);

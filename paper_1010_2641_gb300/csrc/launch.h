@@ -14,6 +14,18 @@ scatter_status launch_prep(scatter_plan_t p, const double* xyz, const float* occ
 // positions must have been prepared by launch_prep on the same stream.
 scatter_status launch_generic(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
 
+// Ordered sum of n_chunks partials [chunk][M] (p->d.partial) with the
+// translation phase, into the outputs (GenericArgs reduction of forward.cu).
+scatter_status launch_generic_reduce(scatter_plan_t p, int n_chunks, float2* amp_out, float* int_out,
+                                     cudaStream_t st);
+
+// Atom-parallel form of the generic sum for short S lists (atompar.cu).
+bool atompar_applicable(const scatter_plan_s* p);
+bool atompar_preferred(const scatter_plan_s* p, const Tiling& s_parallel);
+int atompar_choose_k(const scatter_plan_s* p);
+scatter_status prepare_atompar(scatter_plan_s* p, int K);
+scatter_status launch_atompar(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
+
 // Plain FP64 kernel (no prep needed).
 scatter_status launch_f64(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
                           float* int_out, cudaStream_t st);

@@ -187,6 +187,7 @@ scatter_status apply_tiling(scatter_plan_s* p, const Tiling& t) {
   if (st == SCATTER_OK && n_chunks_per_inst > 1 && p->n_s > 0)
     st = upload<float2>(&p->d.partial, nullptr, (size_t)n_chunks_per_inst * (size_t)p->n_s, &bytes);
   p->tiling_bytes = bytes;
+  if (st == SCATTER_OK && t.atom_k > 0) st = prepare_atompar(p, t.atom_k);
   return st;
 }
 
@@ -232,6 +233,7 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.sep_A);
   release(d.sep_partial);
   release(d.sep_chunks);
+  release(d.ap_blocks);
   release(d.sep_axis_s);
   release(d.sep_axis64);
   release(d.sep_virt);
@@ -439,6 +441,8 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
     if (op && op->threads) t.threads = op->threads;
     if (op && op->points_per_thread) t.R = op->points_per_thread;
     if (op && op->split_k) t.split_k = op->split_k;
+    if (op && (op->threads || op->points_per_thread || op->split_k || op->atoms_per_thread < 0)) t.atom_k = 0;
+    if (op && op->atoms_per_thread > 0) t.atom_k = op->atoms_per_thread;
     if (!generic_tiling_supported(t))
       return fail(SCATTER_ERR_INVALID_ARG, "unsupported tile override (threads=%d R=%d)", t.threads, t.R);
     if ((st = apply_tiling(p.get(), t))) return st;
@@ -447,7 +451,7 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
       if (op && op->autotune && !(op->threads || op->points_per_thread) &&
           (st = autotune_batch(p.get(), op->tune_cache)))
         return st;
-    } else if (op && op->autotune && !(op->threads || op->points_per_thread || op->split_k)) {
+    } else if (op && op->autotune && !(op->threads || op->points_per_thread || op->split_k || op->atoms_per_thread)) {
       if ((st = autotune_generic(p.get(), op->tune_cache))) return st;
     }
   } else {
@@ -457,9 +461,9 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e, "plan synchronize");
   if (log_enabled())
-    fprintf(stderr, "[scatter] plan: path=%d N=%lld slots=%lld M=%lld threads=%d R=%d split_k=%d\n", (int)p->path,
-            (long long)p->n_atoms, (long long)p->n_slots, (long long)p->n_s, p->tiling.threads, p->tiling.R,
-            p->tiling.split_k);
+    fprintf(stderr, "[scatter] plan: path=%d N=%lld slots=%lld M=%lld threads=%d R=%d split_k=%d atom_k=%d\n",
+            (int)p->path, (long long)p->n_atoms, (long long)p->n_slots, (long long)p->n_s, p->tiling.threads,
+            p->tiling.R, p->tiling.split_k, p->tiling.atom_k);
   *out = p.release();
   return SCATTER_OK;
 }

@@ -74,6 +74,7 @@ struct Tiling {
   int threads = 256;
   int R = 8;          // S points per thread
   int split_k = 1;    // atom chunks per S tile
+  int atom_k = 0;     // > 0: atom-parallel form, atoms per thread (atompar.cu)
 };
 
 struct DeviceBuffers {
@@ -113,6 +114,7 @@ struct DeviceBuffers {
   void* sep_A = nullptr;            // A operand blocks (f16 hi/lo)
   float* sep_partial = nullptr;     // [chunk][2][sep_ns] planar
   Segment* sep_chunks = nullptr;    // separable atom chunks: one species each, step-aligned slots
+  Segment* ap_blocks = nullptr;     // atom-parallel blocks: one species each, <= 256 K slots
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
   double* sep_axis64 = nullptr;     // separable grid axes, full S
   float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid
@@ -171,6 +173,7 @@ struct scatter_plan_s {
   int64_t sep_n[3] = {0, 0, 0};                  // separable grid shape (GID: n_h, n_k, 4 n_af)
   int64_t sep_ns = 0;
   int32_t sep_n_chunks = 0;
+  int32_t ap_n_blocks = 0;
   std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
   bool adj_ready = false;
   int adj_split = 1;

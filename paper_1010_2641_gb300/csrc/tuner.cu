@@ -52,6 +52,9 @@ bool cache_lookup(const char* path, const std::string& key, Tiling* t) {
       cand.threads = th;
       cand.R = r;
       cand.split_k = k;
+      const char* d = strstr(line, "\"atom_k\":");  // absent in older caches: S-parallel
+      int ak = 0;
+      if (d && sscanf(d, "\"atom_k\": %d", &ak) == 1 && ak >= 0 && ak <= 16) cand.atom_k = ak;
       if (generic_tiling_supported(cand) && k >= 1 && k <= 256) {
         *t = cand;
         found = true;
@@ -66,8 +69,8 @@ void cache_store(const char* path, const std::string& key, const Tiling& t, doub
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"R\": %d, \"split_k\": %d, \"ms\": %.4f}\n", key.c_str(),
-          t.threads, t.R, t.split_k, ms);
+  fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"R\": %d, \"split_k\": %d, \"atom_k\": %d, \"ms\": %.4f}\n",
+          key.c_str(), t.threads, t.R, t.split_k, t.atom_k, ms);
   fclose(f);
 }
 
@@ -124,6 +127,8 @@ Tiling heuristic_tiling(const scatter_plan_s* p) {
   t.R = 8;
   if (p->s_kind == SCATTER_S_GRID && p->n_axis[2] < 8) t.R = 4;
   t.split_k = best_split(p, t);
+  // short S lists: parallelise over the atoms instead (atompar.cu)
+  if (atompar_preferred(p, t)) t.atom_k = atompar_choose_k(p);
   return t;
 }
 
@@ -140,7 +145,7 @@ scatter_status autotune_generic(scatter_plan_s* p, const char* cache_path) {
   auto add = [&](Tiling c) {
     if (!generic_tiling_supported(c) || c.split_k < 1) return;
     for (const Tiling& o : cands)
-      if (o.threads == c.threads && o.R == c.R && o.split_k == c.split_k) return;
+      if (o.threads == c.threads && o.R == c.R && o.split_k == c.split_k && o.atom_k == c.atom_k) return;
     cands.push_back(c);
   };
   add(start);
@@ -157,6 +162,13 @@ scatter_status autotune_generic(scatter_plan_s* p, const char* cache_path) {
       if ((double)p->n_slots / hi.split_k >= 256) add(hi);
       add(lo);
     }
+  if (atompar_applicable(p))
+    for (int K : {1, 2, 4, 8, 16}) {
+      Tiling c;
+      c.split_k = 1;
+      c.atom_k = K;
+      add(c);
+    }
   double best_ms = 1e30;
   Tiling best = start;
   const double first = time_tiling(p, start, 1);
@@ -165,8 +177,8 @@ scatter_status autotune_generic(scatter_plan_s* p, const char* cache_path) {
   for (size_t i = 0; i < cands.size(); ++i) {
     const double ms = i == 0 ? first : time_tiling(p, cands[i], reps);
     if (log_enabled())
-      fprintf(stderr, "[scatter] autotune threads=%d R=%d split=%d: %.3f ms\n", cands[i].threads, cands[i].R,
-              cands[i].split_k, ms);
+      fprintf(stderr, "[scatter] autotune threads=%d R=%d split=%d atom_k=%d: %.3f ms\n", cands[i].threads,
+              cands[i].R, cands[i].split_k, cands[i].atom_k, ms);
     if (ms < best_ms) {
       best_ms = ms;
       best = cands[i];

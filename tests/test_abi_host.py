@@ -55,13 +55,32 @@ def test_status_strings(L):
     assert L.scatter_status_string(99).decode() == "SCATTER_ERR_UNKNOWN"
 
 
-def test_struct_sizes_match_c_layout():
-    # field-by-field C layout on LP64 (x86_64 and aarch64 alike)
-    assert ctypes.sizeof(B.scatter_species) == 96
-    assert ctypes.sizeof(B.scatter_problem) == 200
-    assert B.scatter_problem.axis.offset == 64 and B.scatter_problem.center_hkl.offset == 120
-    assert B.scatter_problem.atom_off.offset == 184
-    assert ctypes.sizeof(B.scatter_plan_info) == 96
+def test_struct_sizes_match_c_layout(tmp_path):
+    """Every struct of the ABI: ctypes size and field offsets equal what the
+    C compiler makes of include/scatter.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [B.scatter_species, B.scatter_problem, B.scatter_options, B.scatter_plan_info,
+               B.scatter_microbench_result]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "scatter.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("%zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(ctypes.sizeof(st))
+        want += [getattr(st, name).offset for name, _ in st._fields_]
+    assert got == want
 
 
 def _problem(n_atoms=10, n_s=5, species_idx=None, coef=None):
