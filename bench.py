@@ -452,9 +452,10 @@ def measure_paths(args, dev, clk):
     ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
     res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
                            "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr",
-                           "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms,
-                                                  MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk, "Gpair/s",
-                                                  "alu", "pairs (2 MUFU sin/cos each)")}
+                           # uniform l axis: the line kernel carries the phase along l by a complex multiply,
+                           # 8 FMA-pipe ops per pair at 128 lane-ops per SM per clock, no MUFU
+                           "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, clk, "Gpair/s", "alu",
+                                                  "pairs (8 FMA-pipe ops each)")}
     del plan, x, A, I_obs
     # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
     isl = W.truncated_pyramid()

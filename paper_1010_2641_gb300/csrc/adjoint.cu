@@ -22,6 +22,7 @@
 //                 -2 pi w_j and writes the caller's atom order.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cmath>
 #include <vector>
 #include "device_common.cuh"
 #include "launch.h"
@@ -47,7 +48,8 @@ struct LossArgs {
   const float* coef;
   int n_species;
   float inv4a2;
-  float4* table;          // [n_species][M][2]
+  int line;               // 1: compact rows (s_z, S_z, gF.re, gF.im) for k_adjoint_line
+  float4* table;          // [n_species][M][2], or [n_species][M] (line)
   double* loss_part;      // [gridDim.x]
 };
 
@@ -87,9 +89,13 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a)
     const float sx = (float)(S[0] - a.H[0]), sy = (float)(S[1] - a.H[1]), sz = (float)(S[2] - a.H[2]);
     for (int sp = 0; sp < a.n_species; ++sp) {
       const float2 gF = dev::cmul(gp, dev::form_factor(a.coef + kNCoef * sp, s2));
-      float4* row = a.table + 2 * ((int64_t)sp * a.n_s + m);
-      row[0] = make_float4(sx, sy, sz, gF.x);
-      row[1] = make_float4(Sx, Sy, Sz, gF.y);
+      if (a.line) {
+        a.table[(int64_t)sp * a.n_s + m] = make_float4(sz, Sz, gF.x, gF.y);
+      } else {
+        float4* row = a.table + 2 * ((int64_t)sp * a.n_s + m);
+        row[0] = make_float4(sx, sy, sz, gF.x);
+        row[1] = make_float4(Sx, Sy, Sz, gF.y);
+      }
     }
   }
   // deterministic block reduction of the misfit
@@ -223,6 +229,152 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   }
 }
 
+// Grid variant of k_adjoint for an l axis of uniform step ds.  S tiles are
+// segments of one l line (fixed h, k), so s_x, s_y, S_x, S_y are constants
+// of the tile and the table row per point shrinks to (s_z, S_z, gF.re,
+// gF.im).  Along the line the phase advances by ds z'_j per point, so
+// e^{2 i pi phi} is carried from point to point by one complex multiply
+// with w_j = e^{2 i pi ds z'_j} instead of a MUFU sin/cos per pair (four
+// FMA-pipe ops; the pair costs eight in all, no MUFU).  Every 64 points the
+// exponential is re-seeded from the exactly reduced phase, which bounds the
+// rounding drift of the recurrence to ~64 products (~1e-5 relative, against
+// the 1e-3 tolerance of the gradients).  Per tile: FP32 line sums
+// sum v and sum S_z v, folded into the FP64 outer sums as S_x sum v,
+// S_y sum v, sum S_z v.
+struct AdjLineArgs {
+  const float4* atom4;
+  const AdjBlock* blocks;
+  const float4* table;      // [n_species][M]: (s_z, S_z, gF.re, gF.im)
+  const float* axis_s;      // [n0 | n1 | n2] offsets s = axis - H
+  float H[3];
+  int64_t n0, n1, n2;
+  float ds;                 // step of the l axis
+  int64_t lines_per_chunk;
+  float* partial;           // [split][n_slots][3]
+  int64_t n_slots;
+  unsigned* status;
+};
+
+constexpr int kReseed = 64;  // points between exact re-seeds of the recurrence
+
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs a) {
+  __shared__ __align__(128) float4 sh_s[2][kSTile];
+  __shared__ __align__(8) uint64_t sh_bar[2];
+  const int tid = threadIdx.x;
+  const AdjBlock blk = a.blocks[blockIdx.x];
+  const int chunk = blockIdx.y;
+  const int64_t n_lines = a.n0 * a.n1;
+  const int64_t L0 = (int64_t)chunk * a.lines_per_chunk;
+  const int64_t L1 = dev::min64(n_lines, L0 + a.lines_per_chunk);
+  const int64_t segs = (a.n2 + kSTile - 1) / kSTile;  // tiles per line
+  const float4* tab = a.table + (int64_t)blk.species * n_lines * a.n2;
+
+  float x[kAdjRA], y[kAdjRA], z[kAdjRA], c[kAdjRA], wr[kAdjRA], wi[kAdjRA];
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) {
+    const int i = r * kAdjThreads + tid;
+    const float4 at = i < blk.count ? a.atom4[blk.begin + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    x[r] = at.x;
+    y[r] = at.y;
+    z[r] = at.z;
+    c[r] = at.w;
+    float sn, cs;
+    dev::sincos_cycles_mufu(dev::frac_rn(a.ds * z[r]), &sn, &cs);  // rotation per l step
+    wr[r] = cs;
+    wi[r] = sn;
+  }
+  double gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) gx[r] = gy[r] = gz[r] = 0.0;
+
+  if (tid == 0) {
+    dev::mbar_init(&sh_bar[0], 1);
+    dev::mbar_init(&sh_bar[1], 1);
+    dev::mbar_fence_init();
+  }
+  __syncthreads();
+  const int64_t n_tiles = L1 > L0 ? (L1 - L0) * segs : 0;
+  auto issue = [&](int64_t k) {
+    if (k >= n_tiles) return;
+    const int64_t line = L0 + k / segs, j0 = (k % segs) * kSTile;
+    const int cnt = (int)dev::min64(kSTile, a.n2 - j0);
+    const int st = (int)(k & 1);
+    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * 16u);
+    dev::bulk_g2s(&sh_s[st][0], tab + line * a.n2 + j0, (uint32_t)cnt * 16u, &sh_bar[st]);
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  bool aborted = false;
+  for (int64_t k = 0; k < n_tiles; ++k) {
+    const int st = (int)(k & 1);
+    const int64_t line = L0 + k / segs, j0 = (k % segs) * kSTile;
+    const int cnt = (int)dev::min64(kSTile, a.n2 - j0);
+    const bool ok = dev::mbar_wait_bounded(&sh_bar[st], (uint32_t)((k >> 1) & 1));
+    const int64_t i0 = line / a.n1, i1 = line % a.n1;
+    const float sx = a.axis_s[i0], sy = a.axis_s[a.n0 + i1];
+    float base[kAdjRA], er[kAdjRA], ei[kAdjRA], sv[kAdjRA], szv[kAdjRA];
+#pragma unroll
+    for (int r = 0; r < kAdjRA; ++r) {
+      base[r] = fmaf(sy, y[r], fmaf(sx, x[r], c[r]));
+      sv[r] = szv[r] = 0.f;
+    }
+    if (ok) {
+      const float4* sv4 = sh_s[st];
+      for (int jb = 0; jb < cnt; jb += kReseed) {
+        // exact exponential at the first point of every 64
+        const float qz = sv4[jb].x;
+#pragma unroll
+        for (int r = 0; r < kAdjRA; ++r) dev::sincos_cycles_mufu(dev::frac_rn(fmaf(qz, z[r], base[r])), &ei[r], &er[r]);
+        const int je = min(cnt, jb + kReseed);
+#pragma unroll 2
+        for (int j = jb; j < je; ++j) {
+          const float4 q = sv4[j];  // s_z, S_z, gF.re, gF.im
+#pragma unroll
+          for (int r = 0; r < kAdjRA; ++r) {
+            const float v = fmaf(q.z, ei[r], q.w * er[r]);  // Im(gF e)
+            sv[r] += v;
+            szv[r] = fmaf(q.y, v, szv[r]);
+            const float nr = fmaf(er[r], wr[r], -ei[r] * wi[r]);
+            ei[r] = fmaf(er[r], wi[r], ei[r] * wr[r]);
+            er[r] = nr;
+          }
+        }
+      }
+    }
+    const float Sx = a.H[0] + sx, Sy = a.H[1] + sy;
+#pragma unroll
+    for (int r = 0; r < kAdjRA; ++r) {
+      gx[r] += (double)Sx * (double)sv[r];
+      gy[r] += (double)Sy * (double)sv[r];
+      gz[r] += (double)szv[r];
+    }
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      if (tid == 0) {
+        dev::set_status(a.status, kStatusTimeout);
+        for (int64_t kk = k; kk < dev::min64(k + 2, n_tiles); ++kk)
+          dev::mbar_wait_bounded(&sh_bar[kk & 1], (uint32_t)((kk >> 1) & 1), 1LL << 28);
+      }
+      break;
+    }
+    if (tid == 0) issue(k + 2);
+  }
+  if (aborted) return;
+  float* out = a.partial + (int64_t)chunk * a.n_slots * 3;
+#pragma unroll
+  for (int r = 0; r < kAdjRA; ++r) {
+    const int i = r * kAdjThreads + tid;
+    if (i < blk.count) {
+      const int64_t slot = blk.begin + i;
+      out[3 * slot] = (float)gx[r];
+      out[3 * slot + 1] = (float)gy[r];
+      out[3 * slot + 2] = (float)gz[r];
+    }
+  }
+}
+
 __global__ void k_adjoint_final(const float* partial, int split, int64_t n_slots, const int32_t* slot_src,
                                 const float* atom_w, float* grad) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,20 +400,55 @@ scatter_status prepare_adjoint(scatter_plan_s* p) {
   for (const Segment& s : p->all_segs)
     for (int64_t b = s.begin; b < s.end; b += per)
       blocks.push_back(AdjBlock{b, (int32_t)dev::min64(per, s.end - b), s.species});
+  // a grid whose l axis has a uniform step runs the line-recurrence kernel
+  p->adj_line = false;
+  if (p->s_kind == SCATTER_S_GRID && p->n_axis[2] >= 1) {
+    const std::vector<double>& l = p->axis_host[2];
+    const int64_t n2 = (int64_t)l.size();
+    const double ds = n2 > 1 ? (l[n2 - 1] - l[0]) / (double)(n2 - 1) : 0.0;
+    bool uniform = true;
+    for (int64_t i = 0; i < n2 && uniform; ++i)
+      uniform = std::fabs(l[i] - (l[0] + (double)i * ds)) <= 1e-9 * std::max(1.0, std::fabs(l[i]));
+    p->adj_line = uniform;
+    p->adj_ds = (float)ds;
+  }
   // split over S so that the grid fills the GPU a few times over
   int bps = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_adjoint, kAdjThreads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->adj_line ? (const void*)k_adjoint_line
+                                                                      : (const void*)k_adjoint,
+                                                    kAdjThreads, 0) != cudaSuccess) {
     cudaGetLastError();
     bps = 1;
   }
   const int64_t nb = std::max<int64_t>(1, (int64_t)blocks.size());
-  const int64_t target = 4LL * p->n_sm * std::max(1, bps);
-  int64_t split = std::max<int64_t>(1, (target + nb - 1) / nb);
-  int64_t s_per = (p->n_s + split - 1) / split;
-  s_per = std::max<int64_t>(kSTile, (s_per + kSTile - 1) / kSTile * kSTile);
-  split = std::max<int64_t>(1, (p->n_s + s_per - 1) / s_per);
+  const int64_t cap = (int64_t)p->n_sm * std::max(1, bps);  // resident CTAs
+  // S chunks (in whole l lines, or 256-point tiles) per atom block: the split
+  // that minimises waves x work per CTA, among those giving >= 2 waves
+  const int64_t unit = p->adj_line ? p->n_axis[2] : (int64_t)kSTile;
+  const int64_t n_units = p->adj_line ? std::max<int64_t>(1, p->n_axis[0] * p->n_axis[1])
+                                      : std::max<int64_t>(1, (p->n_s + kSTile - 1) / kSTile);
+  int64_t best_per = n_units;
+  double best_cost = 1e300;
+  for (int64_t split = 1; split <= std::min<int64_t>(n_units, 64 * cap / nb + 1); ++split) {
+    const int64_t per = (n_units + split - 1) / split;
+    const int64_t chunks = (n_units + per - 1) / per;
+    const double waves = std::ceil((double)(nb * chunks) / (double)cap);
+    // a fixed per-CTA cost (atom loads, outer sums, partial write) of ~2 units
+    const double cost = waves * (double)(per + 2) + (nb * chunks < 2 * cap ? 1e200 : 0.0);
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best_per = per;
+    }
+  }
+  if (best_cost >= 1e199) best_per = std::max<int64_t>(1, n_units / std::max<int64_t>(1, 2 * cap / nb));
+  const int64_t split = (n_units + best_per - 1) / best_per;
+  if (p->adj_line) {
+    p->adj_lines_per_chunk = best_per;
+    p->adj_s_per_chunk = best_per * unit;
+  } else {
+    p->adj_s_per_chunk = best_per * kSTile;
+  }
   p->adj_split = (int)split;
-  p->adj_s_per_chunk = s_per;
   p->adj_blocks = (int)blocks.size();
   cudaError_t e;
   const size_t tab_bytes = (size_t)p->n_species * (size_t)p->n_s * 2 * sizeof(float4);
@@ -315,6 +502,7 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
   la.coef = p->d.coef;
   la.n_species = grad ? p->n_species : 0;
   la.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
+  la.line = grad && p->adj_line;
   la.table = p->d.adj_table;
   la.loss_part = p->d.loss_part;
   k_loss_weights<<<kLossParts, kLossThreads, 0, st>>>(la);
@@ -336,7 +524,25 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
     if (p->adj_blocks > 0) {
       dim3 gridd((unsigned)p->adj_blocks, (unsigned)p->adj_split);
       timing_begin(p, st);
-      k_adjoint<<<gridd, kAdjThreads, 0, st>>>(aa);
+      if (p->adj_line) {
+        AdjLineArgs al{};
+        al.atom4 = p->d.atom4;
+        al.blocks = p->d.adj_blocks;
+        al.table = p->d.adj_table;
+        al.axis_s = p->d.axis_s;
+        for (int d = 0; d < 3; ++d) al.H[d] = (float)p->inst[0].H[d];
+        al.n0 = p->n_axis[0];
+        al.n1 = p->n_axis[1];
+        al.n2 = p->n_axis[2];
+        al.ds = p->adj_ds;
+        al.lines_per_chunk = p->adj_lines_per_chunk;
+        al.partial = p->d.adj_partial;
+        al.n_slots = p->n_slots;
+        al.status = p->d.status;
+        k_adjoint_line<<<gridd, kAdjThreads, 0, st>>>(al);
+      } else {
+        k_adjoint<<<gridd, kAdjThreads, 0, st>>>(aa);
+      }
       timing_end(p, st);
       p->last_launches += 1;
     }

@@ -124,7 +124,7 @@ struct DeviceBuffers {
   int* counter = nullptr;
   // adjoint workspace (allocated on first backward)
   AdjBlock* adj_blocks = nullptr;
-  float4* adj_table = nullptr;      // [n_species][M][2]
+  float4* adj_table = nullptr;      // [n_species][M][2], or [n_species][M] in line mode
   float* adj_partial = nullptr;     // [split][n_slots][3]
 };
 
@@ -179,4 +179,7 @@ struct scatter_plan_s {
   int adj_split = 1;
   int adj_blocks = 0;
   int64_t adj_s_per_chunk = 0;
+  bool adj_line = false;            // uniform-l grid: k_adjoint_line (phase recurrence)
+  float adj_ds = 0.f;               // its l step
+  int64_t adj_lines_per_chunk = 0;
 };

@@ -130,3 +130,29 @@ def test_strained_cube_full_grid_properties():
     g = grad.double()
     assert torch.all(torch.isfinite(g))
     assert (g.sum(0).abs().max() / g.abs().sum()).item() < 1e-4
+
+
+@pytest.mark.parametrize("l_axis", ["long_uniform", "non_uniform"])
+def test_gradient_line_recurrence_and_fallback(l_axis):
+    """A uniform l axis longer than one 256-point tile runs the line kernel
+    (phase carried along l by a complex multiply, re-seeded every 64 points,
+    several tiles per line); a non-uniform l axis falls back to the table
+    kernel.  Both against the oracle's analytic gradient."""
+    c = W.fcc_sphere(radius_cells=2.6, seed=21)
+    if l_axis == "long_uniform":
+        l = W.linspace_axis(4.0, 300, step=0.004)
+    else:
+        t = np.linspace(-1.0, 1.0, 37)
+        l = 4.0 + 0.3 * np.sign(t) * np.abs(t) ** 1.7
+    axes = [W.linspace_axis(0.0, 3, step=0.02), W.linspace_axis(0.0, 2, step=0.02), l]
+    S = W.grid_points(axes)
+    pert = W.perturbed_copy(c, 0.03, seed=22)
+    I_obs = (np.abs(oracle.amplitude(pert.xyz, S, c.coef, A_LAT, species=c.species)) ** 2).astype(np.float32)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    x = dev(c.xyz)
+    A = plan.amplitude(x)
+    loss, grad = plan.backward(x, A, dev(I_obs, torch.float32))
+    plan.check()
+    L_ref, g_ref = oracle.loss_grad(c.xyz, S, I_obs, c.coef, A_LAT, species=c.species)
+    assert abs(loss.item() - L_ref) < 1e-4 * L_ref
+    assert rel_l2(grad.cpu().numpy(), g_ref) < TOL_GRAD
