@@ -57,6 +57,7 @@ def _load():
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.oracle_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P]
         lib.oracle_form_factor.argtypes = [P, f64, P, P]
+        lib.oracle_amplitude_table.argtypes = [i64, P, P, P, i32, P, i64, P, P]
         lib.oracle_fresnel.argtypes = [f64, f64, f64, P, P]
         lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
@@ -114,6 +115,24 @@ def amplitude(xyz, S, coef, lattice_a, species=None, occ=None) -> np.ndarray:
     out = np.zeros((S.shape[0], 2))
     _load().oracle_amplitude(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
                              float(lattice_a), S.shape[0], _ptr(S), _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def amplitude_table(xyz, S, table, types=None, occ=None) -> np.ndarray:
+    """Eq. 4: A(S) = sum_j w_j F_{t(j)}(S) exp(2 i pi S.r_j) with a complex
+    factor table F [n_types, M] (block structure factors)."""
+    xyz = _f64(xyz, 3)
+    n = xyz.shape[0]
+    t = None if types is None else np.ascontiguousarray(np.asarray(types, dtype=np.int32).reshape(n))
+    w = None if occ is None else _f64(occ).reshape(n)
+    S = _f64(S, 3)
+    tab = np.asarray(table, dtype=np.complex128).reshape(-1, S.shape[0])
+    if t is not None and n and (t.min() < 0 or t.max() >= tab.shape[0]):
+        raise ValueError("type index out of range")
+    tab2 = np.ascontiguousarray(np.stack([tab.real, tab.imag], -1))
+    out = np.zeros((S.shape[0], 2))
+    _load().oracle_amplitude_table(n, _ptr(xyz), _ptr(t), _ptr(w), tab.shape[0], _ptr(tab2), S.shape[0], _ptr(S),
+                                   _ptr(out))
     return out[:, 0] + 1j * out[:, 1]
 
 

@@ -94,6 +94,37 @@ void oracle_amplitude(int64_t n_atoms, const double* xyz, const int32_t* species
 }
 
 /*
+ * Eq. 4: scattering from blocks of atoms (groups of unit cells), each block j
+ * of type t(j) with its own structure factor F_t(S) at every reflection:
+ *   A(S_m) = sum_j w_j F_{t(j)}(S_m) exp(2 i pi S_m.r_j),
+ * r_j = r_j^0 + u_j the displaced block origin.  F is given as a table
+ * [n_types][n_s][2] (re, im) of the caller's (for single-atom blocks it is
+ * f_t(|S|), and the sum is Eq. 2).
+ */
+void oracle_amplitude_table(int64_t n_atoms, const double* xyz, const int32_t* types,
+                            const double* occ, int32_t n_types, const double* table,
+                            int64_t n_s, const double* S, double* A) {
+  (void)n_types;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t m = 0; m < n_s; ++m) {
+    const double* Sm = S + 3 * m;
+    double are = 0.0, aim = 0.0;
+    for (int64_t j = 0; j < n_atoms; ++j) {
+      const double* r = xyz + 3 * j;
+      const double phase = 2.0 * kPi * (Sm[0] * r[0] + Sm[1] * r[1] + Sm[2] * r[2]);
+      const double c = cos(phase), s = sin(phase);
+      const double w = occ ? occ[j] : 1.0;
+      const int32_t t = types ? types[j] : 0;
+      const double fr = table[2 * (t * n_s + m)], fi = table[2 * (t * n_s + m) + 1];
+      are += w * (fr * c - fi * s);
+      aim += w * (fr * s + fi * c);
+    }
+    A[2 * m] = are;
+    A[2 * m + 1] = aim;
+  }
+}
+
+/*
  * Fresnel reflection and transmission coefficients of the substrate surface
  * (Section 3, pynx.gid; Section 4.3) for a wave in vacuum meeting a medium of
  * index n = 1 - delta + i beta at grazing angle alpha (rad):

@@ -330,3 +330,63 @@ def test_gradient_translation_invariance():
     I_obs = rng.uniform(0, 1e4, 150)
     L, g = oracle.loss_grad(c.xyz, S, I_obs, c.coef, A_LAT, c.species)
     assert np.max(np.abs(g.sum(0))) < 1e-10 * np.sum(np.abs(g))
+
+
+# --- Eq. 4: blocks of atoms with per-(type, S) structure factors ------------
+
+def _fcc_block():
+    """The four atoms of an fcc cell, in lattice units (the block's content)."""
+    return np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]], dtype=np.float64)
+
+
+def test_table_of_form_factors_reproduces_eq2():
+    """Single-atom 'blocks' with F_t(S) = f_t(|S|): Eq. 4 is Eq. 2.  Two types
+    and a spread of |S| catch a transposed table index or a swapped product."""
+    rng = np.random.default_rng(40)
+    xyz = rng.uniform(-6, 6, (97, 3))
+    types = (rng.uniform(size=97) < 0.4).astype(np.int32)
+    S = rng.uniform(-3, 3, (33, 3)) + np.array([0, 0, 4.0])
+    coef = W.si_ge_species()
+    q = np.linalg.norm(S, axis=1) / W.LATTICE_A
+    table = np.array([[oracle.form_factor(coef[t], qq) for qq in q] for t in range(2)])
+    got = oracle.amplitude_table(xyz, S, table, types=types)
+    ref = oracle.amplitude(xyz, S, coef, W.LATTICE_A, species=types)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_blocks_of_fcc_cells_equal_the_atom_sum():
+    """A displaced lattice of fcc-cell blocks (two block types with different
+    content weights) against Eq. 2 over every atom of every block: the block
+    structure factor F_t(S) = sum_a f e^{2 i pi S.rho_a} makes Eq. 4 exact."""
+    rng = np.random.default_rng(41)
+    cells = np.stack(np.meshgrid(np.arange(4), np.arange(3), np.arange(5), indexing="ij"), -1).reshape(-1, 3)
+    R = cells + rng.normal(0, 0.03, cells.shape)          # r_j^0 + u_j
+    btype = (rng.uniform(size=len(R)) < 0.3).astype(np.int32)
+    rho = _fcc_block()
+    S = rng.uniform(-0.5, 0.5, (41, 3)) + np.array([1.0, 1.0, 3.0])
+    coef = W.si_ge_species()
+    q = np.linalg.norm(S, axis=1) / W.LATTICE_A
+    f = np.array([[oracle.form_factor(coef[t], qq) for qq in q] for t in range(2)])       # [type, M]
+    geo = np.exp(2j * np.pi * (S @ rho.T))                                                 # [M, 4]
+    table = f * geo.sum(1)[None, :]
+    got = oracle.amplitude_table(R, S, table, types=btype)
+    atoms = (R[:, None, :] + rho[None, :, :]).reshape(-1, 3)
+    species = np.repeat(btype, len(rho))
+    ref = oracle.amplitude(atoms, S, coef, W.LATTICE_A, species=species)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_table_occupancy_and_duplication():
+    rng = np.random.default_rng(42)
+    xyz = rng.uniform(-4, 4, (20, 3))
+    S = rng.uniform(-1, 1, (9, 3))
+    table = rng.normal(size=(1, 9)) + 1j * rng.normal(size=(1, 9))
+    w = np.ones(20)
+    w[3] = 2.0
+    w[7] = 0.0
+    dup = np.concatenate([xyz, xyz[3:4]])
+    keep = np.ones(21, dtype=bool)
+    keep[7] = False
+    a = oracle.amplitude_table(xyz, S, table, occ=w)
+    b = oracle.amplitude_table(dup[keep], S, table)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
