@@ -133,6 +133,15 @@ typedef struct scatter_problem {
   int32_t batch;                   /* 1, or number of instances               */
   const int64_t* atom_off;         /* [batch+1] when batch > 1, else NULL     */
   const int64_t* s_off;            /* [batch+1] when batch > 1, else NULL     */
+
+  /* Blocks of atoms (Eq. 4): host complex128 [n_species][M] (re, im pairs),
+   * M the output points in output order.  When set, the "species" are
+   * block types and F_t(S_m) = factor_table[t][m] replaces the Gaussian
+   * form factor (the species coefficients are then unused); positions are
+   * the displaced block origins.  LIST and GRID plans of one instance,
+   * forward only (scatter_backward/scatter_vjp return UNSUPPORTED).
+   * Copied at plan time.  NULL: the form factors of `species`.            */
+  const double* factor_table;
 } scatter_problem;
 
 /* Plan options.  Zero-initialised options mean "automatic". */

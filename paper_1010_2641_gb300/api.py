@@ -53,6 +53,9 @@ class Plan:
     center : reference reflection H (integers) or None (automatic).
     gid : dict(wavelength=, alpha_i=, delta=, beta=) for grazing incidence.
     atom_off, s_off : batch CSR offsets (lists only).
+    factor_table : [n_species, M] complex (Eq. 4, blocks of atoms): the
+        "species" are block types with structure factors F_t(S_m) given per
+        output point; positions are the displaced block origins.
     atoms_per_thread : generic path, one instance: 1/2/4/8/16 forces the
         atom-parallel form (for many atoms and few reflections), 0 lets the
         heuristic or autotuner choose, -1 keeps the S-parallel kernel.
@@ -62,7 +65,7 @@ class Plan:
                  atom_species=None, center=None, path: str = "auto", gid: dict | None = None,
                  atom_off=None, s_off=None, autotune: bool = False, tune_cache: str | None = None,
                  threads: int = 0, points_per_thread: int = 0, split_k: int = 0, use_graph: bool = True,
-                 timing: bool = False, atoms_per_thread: int = 0):
+                 timing: bool = False, atoms_per_thread: int = 0, factor_table=None):
         L = B.lib()
         self._keep = []
         pr = B.scatter_problem()
@@ -114,6 +117,12 @@ class Plan:
             pr.batch = ao.shape[0] - 1
             pr.atom_off = ao.ctypes.data
             pr.s_off = so.ctypes.data
+        if factor_table is not None:
+            m = int(np.prod(self.shape))
+            ft = np.asarray(factor_table, dtype=np.complex128).reshape(coef.shape[0], m)
+            ft2 = np.ascontiguousarray(np.stack([ft.real, ft.imag], -1))
+            self._keep.append(ft2)
+            pr.factor_table = ft2.ctypes.data
         op = B.scatter_options()
         op.path = _PATHS[path]
         op.autotune = int(bool(autotune))

@@ -65,6 +65,7 @@ class scatter_problem(ctypes.Structure):
         ("batch", c_int32),
         ("atom_off", c_void_p),
         ("s_off", c_void_p),
+        ("factor_table", c_void_p),
     ]
 
 

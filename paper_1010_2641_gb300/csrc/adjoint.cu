@@ -473,6 +473,7 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
                                cudaStream_t st) {
   if (p->path == SCATTER_PATH_FP64_REF)
     return fail(SCATTER_ERR_UNSUPPORTED, "backward runs on the generic path; plan with SCATTER_PATH_GENERIC");
+  if (p->d.ftab) return fail(SCATTER_ERR_UNSUPPORTED, "backward with a factor table (Eq. 4 blocks) is not available");
   scatter_status s = SCATTER_OK;
   if (grad) {
     if ((s = prepare_adjoint(p)) != SCATTER_OK) return s;

@@ -36,6 +36,7 @@ struct ApArgs {
   int grid_mode;
   float H[3];
   float inv4a2;
+  const float2* ftab;     // Eq. 4 factor table [n_species][M], or null (form factors)
   float2* partial;        // [block][M]
 };
 
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
     }
     const float4 s = sh_s[i];
     const float Sx = a.H[0] + s.x, Sy = a.H[1] + s.y, Sz = a.H[2] + s.z;
-    const float2 F = dev::form_factor(cf, (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2);
+    const float2 F = a.ftab ? a.ftab[(int64_t)blk.species * a.n_s + p0 + i]
+                            : dev::form_factor(cf, (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2);
     a.partial[(int64_t)blockIdx.y * a.n_s + p0 + i] = dev::cmul(F, v);
   }
 }
@@ -213,6 +215,7 @@ scatter_status launch_atompar(scatter_plan_t p, float2* amp_out, float* int_out,
   a.grid_mode = p->s_kind == SCATTER_S_GRID;
   for (int d = 0; d < 3; ++d) a.H[d] = (float)p->inst[0].H[d];
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
+  a.ftab = p->d.ftab;
   a.partial = p->d.partial;
   dim3 grid((unsigned)((p->n_s + kApPts - 1) / kApPts), (unsigned)p->ap_n_blocks);
   void* args[] = {&a};

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
     const int chunk = in.chunk0 + w.chunk;
     float2 tot[R];
     if (!chunk_sum<kModeList, R>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk], a.chunk_seg_off[chunk + 1],
-                                 a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status))
+                                 a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status, nullptr,
+                                 1, 0, 0))  // batches take no factor table
       return;
     const int64_t M_b = in.s_end - in.s_begin;
     const double* t = a.inst_shift + 3 * w.inst;

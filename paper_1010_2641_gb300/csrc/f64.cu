@@ -16,6 +16,7 @@ struct F64Args {
   const int32_t* inst_seg_off;  // [batch+1] segment range of each instance
   const int32_t* s_inst;        // LIST batch: instance of each point, or null
   const double* coef64;
+  const double* ftab64;         // Eq. 4 factor table [n_species][M][2], or null
   int64_t n_s;
   const double* S64;            // LIST [M][3]
   const double* axis64;         // GRID [n0 | n1 | n2]
@@ -54,7 +55,12 @@ __global__ void __launch_bounds__(128) k_f64(const F64Args a) {
   for (int g = a.inst_seg_off[b]; g < a.inst_seg_off[b + 1]; ++g) {
     const Segment sg = a.segs[g];
     double fr, fi;
-    form_factor64(a.coef64 + kNCoef * sg.species, s2, &fr, &fi);
+    if (a.ftab64) {
+      fr = a.ftab64[2 * ((int64_t)sg.species * a.n_s + m)];
+      fi = a.ftab64[2 * ((int64_t)sg.species * a.n_s + m) + 1];
+    } else {
+      form_factor64(a.coef64 + kNCoef * sg.species, s2, &fr, &fi);
+    }
     double tr = 0.0, ti = 0.0;
     for (int64_t slot = sg.begin; slot < sg.end; ++slot) {
       const int32_t j = a.slot_src[slot];
@@ -85,6 +91,7 @@ scatter_status launch_f64(scatter_plan_t p, const double* xyz, const float* occ,
   a.inst_seg_off = p->d.chunk_seg_off;  // one chunk per instance on this path
   a.s_inst = p->d.s_inst;
   a.coef64 = p->d.coef64;
+  a.ftab64 = p->d.ftab64;
   a.n_s = p->n_s;
   a.S64 = p->d.S64;
   a.axis64 = p->d.axis64;

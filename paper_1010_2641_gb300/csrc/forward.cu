@@ -195,10 +195,14 @@ __global__ void __launch_bounds__(THREADS) k_generic(const GenericArgs a) {
     dev::mbar_fence_init();
   }
   __syncthreads();
+  // output index of point r: pbase + r pstride (for a factor table)
+  const int64_t pbase = MODE == kModeGrid ? idx0 : idx0 + tid;
+  const int64_t pstride = MODE == kModeGrid ? 1 : THREADS;
   float2 tot[R];
   int k = 0;
   if (!chunk_sum<MODE, R>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk], a.chunk_seg_off[chunk + 1], a.coef,
-                          a.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status))
+                          a.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase,
+                          pstride))
     return;
 
   // ---- epilogue -----------------------------------------------------------------
@@ -313,6 +317,7 @@ GenericArgs make_args(scatter_plan_t p) {
   }
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.shift = p->d.inst_shift;
+  a.ftab = p->d.ftab;
   a.status = p->d.status;
   return a;
 }

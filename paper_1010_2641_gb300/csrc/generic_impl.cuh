@@ -26,6 +26,7 @@ struct GenericArgs {
   double H64[3];
   float inv4a2;
   const double* shift;    // [3] device, written by prep
+  const float2* ftab;     // Eq. 4 factor table [n_species][M], or null (form factors)
   float2* out_amp;
   float* out_int;
   float2* partial;        // split-K partials [chunk][M] (or null)
@@ -39,7 +40,9 @@ scatter_status launch_generic_args(GenericArgs a, int R, int threads, int n_chun
 // S points of this thread: atom tiles are staged in shared memory by the TMA
 // engine (two stages, mbarrier completion, bounded waits), the per-pair work
 // is the split phase + MUFU sincos + 2 FFMA into tile-blocked FP32 sums, and
-// f_s(|S|) is folded in at the end of every species segment.  `k` counts the
+// f_s(|S|) is folded in at the end of every species segment (or, with an
+// Eq. 4 factor table, F_s(S) at the thread's point indices pbase + r pstride,
+// clamped to the map).  `k` counts the
 // tiles this CTA has consumed so far (it sets the stage and mbarrier parity
 // and carries over between chunks of a persistent CTA).  Returns false if a
 // wait gave up (the CTA then drains its copies and must stop).
@@ -49,7 +52,8 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
                                           const float* __restrict__ coef, const float H[3], float inv4a2,
                                           const float (&sx)[R], const float (&sy)[R], const float (&sz)[R],
                                           float4 (*sh_atom)[kTile], float (*sh_w)[kTile], uint64_t* sh_bar, int& k,
-                                          float2 (&tot)[R], unsigned* status) {
+                                          float2 (&tot)[R], unsigned* status, const float2* __restrict__ ftab,
+                                          int64_t n_s, int64_t pbase, int64_t pstride) {
   const int tid = threadIdx.x;
   // loader state (used by thread 0 only)
   int l_seg = seg_lo;
@@ -125,7 +129,8 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
       for (int r = 0; r < R; ++r) {
         const float Sx = H[0] + sx[r], Sy = H[1] + sy[r], Sz = H[2] + sz[r];
         const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * inv4a2;
-        const float2 F = dev::form_factor(cf, s2);
+        const float2 F = ftab ? ftab[(int64_t)segs[c_seg].species * n_s + dev::min64(pbase + r * pstride, n_s - 1)]
+                              : dev::form_factor(cf, s2);
         const float2 v = dev::cmul(F, sacc[r]);
         tot[r].x += v.x;
         tot[r].y += v.y;

@@ -109,6 +109,15 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
       if (pr->atom_off[b + 1] < pr->atom_off[b] || pr->s_off[b + 1] < pr->s_off[b])
         return fail(SCATTER_ERR_INVALID_ARG, "batch offsets must be non-decreasing");
   }
+  if (pr->factor_table) {
+    if (pr->s_kind == SCATTER_S_GID_GRID)
+      return fail(SCATTER_ERR_UNSUPPORTED, "a factor table needs a LIST or GRID plan (one factor per point)");
+    if (pr->batch > 1) return fail(SCATTER_ERR_UNSUPPORTED, "a factor table needs a single instance");
+    const int64_t M = pr->s_kind == SCATTER_S_LIST ? pr->n_s : pr->n_axis[0] * pr->n_axis[1] * pr->n_axis[2];
+    for (int64_t i = 0; i < 2 * M * (int64_t)pr->n_species; ++i)
+      if (!std::isfinite(pr->factor_table[i]))
+        return fail(SCATTER_ERR_INVALID_ARG, "factor_table has non-finite values");
+  }
   if (op) {
     if (op->path < SCATTER_PATH_AUTO || op->path > SCATTER_PATH_FP64_REF)
       return fail(SCATTER_ERR_INVALID_ARG, "unknown path %d", op->path);
@@ -234,6 +243,8 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.sep_partial);
   release(d.sep_chunks);
   release(d.ap_blocks);
+  release(d.ftab);
+  release(d.ftab64);
   release(d.sep_axis_s);
   release(d.sep_axis64);
   release(d.sep_virt);
@@ -417,6 +428,15 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
       }
     if ((st = upload(&d.axis_s, ax.data(), ax.size(), &bytes))) return st;
     if ((st = upload(&d.axis64, ax64.data(), ax64.size(), &bytes))) return st;
+  }
+  // Eq. 4 factor table (block structure factors), FP32 and FP64 copies
+  if (pr->factor_table && p->n_s > 0) {
+    const size_t n = (size_t)pr->n_species * (size_t)p->n_s;
+    std::vector<float2> t32(n);
+    for (size_t i = 0; i < n; ++i)
+      t32[i] = make_float2((float)pr->factor_table[2 * i], (float)pr->factor_table[2 * i + 1]);
+    if ((st = upload(&d.ftab, t32.data(), n, &bytes))) return st;
+    if ((st = upload(&d.ftab64, pr->factor_table, 2 * n, &bytes))) return st;
   }
   // backward workspace (g(S) and per-block loss partials)
   if (p->n_s > 0) {

@@ -115,6 +115,8 @@ struct DeviceBuffers {
   float* sep_partial = nullptr;     // [chunk][2][sep_ns] planar
   Segment* sep_chunks = nullptr;    // separable atom chunks: one species each, step-aligned slots
   Segment* ap_blocks = nullptr;     // atom-parallel blocks: one species each, <= 256 K slots
+  float2* ftab = nullptr;           // Eq. 4 factor table [n_species][M], or null (form factors)
+  double* ftab64 = nullptr;         // the same in FP64 (re, im) for the FP64 kernel
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
   double* sep_axis64 = nullptr;     // separable grid axes, full S
   float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid

@@ -486,7 +486,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 // Sum over the chunks in order of f_s(|S|) x T_chunk (Eq. 2: each chunk holds
 // one species s), translation phase, outputs.
 __global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* __restrict__ chunks, int n_chunks,
-                             const float* __restrict__ coef, float inv4a2, int64_t n_s,
+                             const float* __restrict__ coef, const float2* __restrict__ ftab, float inv4a2, int64_t n_s,
                              const double* __restrict__ axis64, int64_t n0, int64_t n1, int64_t n2, double H0,
                              double H1, double H2, const double* __restrict__ shift, float2* out_amp, float* out_int) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -499,7 +499,7 @@ __global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* _
   for (int c = 0; c < n_chunks; ++c) {
     const int sp = chunks[c].species;
     if (sp != cur) {
-      F = dev::form_factor(coef + kNCoef * sp, s2);
+      F = ftab ? ftab[(int64_t)sp * n_s + m] : dev::form_factor(coef + kNCoef * sp, s2);
       cur = sp;
     }
     const float re = partial[(int64_t)c * 2 * n_s + m], im = partial[(int64_t)c * 2 * n_s + n_s + m];
@@ -672,7 +672,8 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
-      p->d.sep_partial, p->d.sep_chunks, n_chunks, p->d.coef, (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
+      p->d.sep_partial, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
+      (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
       p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
       p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, gid ? p->d.sep_virt : amp_out,
       gid ? nullptr : int_out);

@@ -281,3 +281,36 @@ def random_sweep(n_atoms: int, n_s: int, seed: int = 0, box: float = 100.0, cent
     xyz = rng.uniform(0.0, box, (n_atoms, 3))
     S = np.asarray(center, float) + rng.uniform(-0.5, 0.5, (n_s, 3))
     return xyz, S
+
+
+@dataclasses.dataclass
+class BlockModel:
+    """Eq. 4 input: blocks of atoms on a lattice, displaced (r_j^0 + u_j).
+
+    origins : [n_blocks, 3] displaced block origins (lattice units)
+    types   : [n_blocks] block type (0 or 1)
+    content : [n_types] list of [n_atoms_in_block, 3] atom offsets in a block
+    species : [n_types] list of per-atom species indices of each block type
+    """
+    origins: np.ndarray
+    types: np.ndarray
+    content: list
+    species: list
+
+
+def fcc_cell_blocks(n=(12, 12, 8), frac_type1: float = 0.3, amplitude: float = 0.05, sigma: float = 0.01,
+                    seed: int = 5001) -> BlockModel:
+    """A lattice of one-cell fcc blocks (4 atoms each), the block type drawn
+    at random (type 0: Si-like atoms, type 1: Ge-like atoms), displaced by a
+    smooth field u_z = amplitude sin(2 pi x / n_x) plus seeded noise: the
+    continuum-elasticity picture of Section 2.1 at one-cell resolution."""
+    rng = np.random.default_rng(seed)
+    cells = np.stack(np.meshgrid(*[np.arange(k, dtype=np.float64) for k in n], indexing="ij"), -1).reshape(-1, 3)
+    cells -= 0.5 * (np.asarray(n, dtype=np.float64) - 1.0)
+    u = np.zeros_like(cells)
+    u[:, 2] = amplitude * np.sin(2.0 * np.pi * cells[:, 0] / n[0])
+    u += rng.normal(0.0, sigma, cells.shape)
+    types = (rng.uniform(size=len(cells)) < frac_type1).astype(np.int32)
+    cell = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]], dtype=np.float64)
+    return BlockModel(origins=cells + u, types=types, content=[cell, cell],
+                      species=[np.zeros(4, np.int32), np.ones(4, np.int32)])
