@@ -58,6 +58,7 @@ def _load():
         lib.oracle_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P]
         lib.oracle_form_factor.argtypes = [P, f64, P, P]
         lib.oracle_amplitude_table.argtypes = [i64, P, P, P, i32, P, i64, P, P]
+        lib.oracle_fft_approx.argtypes = [i64, P, P, P, i32, P, f64, P, f64, P, i64, P, P]
         lib.oracle_fresnel.argtypes = [f64, f64, f64, P, P]
         lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
@@ -133,6 +134,19 @@ def amplitude_table(xyz, S, table, types=None, occ=None) -> np.ndarray:
     out = np.zeros((S.shape[0], 2))
     _load().oracle_amplitude_table(n, _ptr(xyz), _ptr(t), _ptr(w), tab.shape[0], _ptr(tab2), S.shape[0], _ptr(S),
                                    _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def fft_approx(xyz, S, coef, lattice_a, H, step, origin, species=None, occ=None) -> np.ndarray:
+    """Eq. 5/6: atoms on the nearest node R_j of a grid of step `step` from
+    `origin`, exp(2 i pi (S-H).u_j) dropped, as a direct sum at S [M, 3]."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    S = _f64(S, 3)
+    Hv = _f64(np.asarray(H, dtype=np.float64), 3).reshape(3)
+    ov = _f64(np.asarray(origin, dtype=np.float64), 3).reshape(3)
+    out = np.zeros((S.shape[0], 2))
+    _load().oracle_fft_approx(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                              float(lattice_a), _ptr(Hv), float(step), _ptr(ov), S.shape[0], _ptr(S), _ptr(out))
     return out[:, 0] + 1j * out[:, 1]
 
 

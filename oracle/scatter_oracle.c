@@ -125,6 +125,44 @@ void oracle_amplitude_table(int64_t n_atoms, const double* xyz, const int32_t* t
 }
 
 /*
+ * Eq. 5/6: the FFT approximation.  Every atom is put on the nearest node R_j
+ * of a grid of step d (lattice units) from `origin`, r_j = R_j + u_j, and
+ * the factor exp(2 i pi (S - H).u_j) is dropped, which is exact when
+ * (S - H).u_j = 0 and a good approximation while |(S - H).u_j| << 1
+ * (Eq. 7):
+ *   A(S) ~ sum_j w_j f_{s(j)}(|S|) exp(2 i pi H.r_j) exp(2 i pi (S - H).R_j),
+ * written here as that sum itself (no transform), for the reflections S.
+ */
+void oracle_fft_approx(int64_t n_atoms, const double* xyz, const int32_t* species,
+                       const double* occ, int32_t n_species, const double* coef,
+                       double lattice_a, const double* H, double step, const double* origin,
+                       int64_t n_s, const double* S, double* A) {
+  (void)n_species;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t m = 0; m < n_s; ++m) {
+    const double* Sm = S + 3 * m;
+    const double q = s_norm(Sm, lattice_a);
+    double are = 0.0, aim = 0.0;
+    for (int64_t j = 0; j < n_atoms; ++j) {
+      const double* r = xyz + 3 * j;
+      double R[3];
+      for (int d = 0; d < 3; ++d) R[d] = origin[d] + step * nearbyint((r[d] - origin[d]) / step);
+      const double phase = 2.0 * kPi * (H[0] * r[0] + H[1] * r[1] + H[2] * r[2] +
+                                        (Sm[0] - H[0]) * R[0] + (Sm[1] - H[1]) * R[1] + (Sm[2] - H[2]) * R[2]);
+      const double c = cos(phase), s = sin(phase);
+      const double w = occ ? occ[j] : 1.0;
+      const int32_t sp = species ? species[j] : 0;
+      double fr, fi;
+      oracle_form_factor(coef + ORACLE_NCOEF * sp, q, &fr, &fi);
+      are += w * (fr * c - fi * s);
+      aim += w * (fr * s + fi * c);
+    }
+    A[2 * m] = are;
+    A[2 * m + 1] = aim;
+  }
+}
+
+/*
  * Fresnel reflection and transmission coefficients of the substrate surface
  * (Section 3, pynx.gid; Section 4.3) for a wave in vacuum meeting a medium of
  * index n = 1 - delta + i beta at grazing angle alpha (rad):

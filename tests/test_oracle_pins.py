@@ -390,3 +390,47 @@ def test_table_occupancy_and_duplication():
     a = oracle.amplitude_table(xyz, S, table, occ=w)
     b = oracle.amplitude_table(dup[keep], S, table)
     assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+# --- Eq. 5/6: the FFT approximation (atoms on grid nodes, (S-H).u dropped) --
+
+def _grid_crystal(seed, sigma):
+    rng = np.random.default_rng(seed)
+    nodes = np.stack(np.meshgrid(np.arange(6), np.arange(5), np.arange(4), indexing="ij"), -1).reshape(-1, 3) * 0.5
+    return nodes + rng.normal(0, sigma, nodes.shape), nodes
+
+
+def test_fft_approx_exact_on_the_nodes():
+    """u_j = 0: nothing is dropped, Eq. 5/6 is Eq. 2 (any S, not only the FFT grid)."""
+    xyz, _ = _grid_crystal(50, 0.0)
+    S = np.random.default_rng(51).uniform(-0.4, 0.4, (23, 3)) + np.array([0, 0, 4.0])
+    coef = W.si_ge_species()
+    sp = (np.arange(len(xyz)) % 3 == 0).astype(np.int32)
+    got = oracle.fft_approx(xyz, S, coef, W.LATTICE_A, [0, 0, 4], 0.5, [0, 0, 0], species=sp)
+    ref = oracle.amplitude(xyz, S, coef, W.LATTICE_A, species=sp)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_fft_approx_without_reference_is_eq2_on_the_nodes():
+    """H = 0: the phase is S.R_j, Eq. 2 of the snapped positions (catches r used for R)."""
+    xyz, nodes = _grid_crystal(52, 0.06)
+    S = np.random.default_rng(53).uniform(-0.4, 0.4, (19, 3))
+    coef = W.si_ge_species()
+    got = oracle.fft_approx(xyz, S, coef, W.LATTICE_A, [0, 0, 0], 0.5, [0, 0, 0])
+    ref = oracle.amplitude(nodes, S, coef, W.LATTICE_A)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_fft_approx_error_within_the_dropped_phase_bound():
+    """|A_approx - A| <= sum_j |w_j f_j| 2 pi |(S - H).u_j| (|e^{ix} - 1| <= |x|), pointwise;
+    a wrong H term (H.R for H.r) breaks it at H = (0, 0, 4)."""
+    xyz, nodes = _grid_crystal(54, 0.03)
+    H = np.array([0.0, 0.0, 4.0])
+    S = H + np.random.default_rng(55).uniform(-0.05, 0.05, (31, 3))
+    coef = W.unit_species()
+    got = oracle.fft_approx(xyz, S, coef, W.LATTICE_A, H, 0.5, [0, 0, 0])
+    ref = oracle.amplitude(xyz, S, coef, W.LATTICE_A)
+    u = xyz - nodes
+    bound = 2 * np.pi * np.abs((S - H) @ u.T).sum(1)
+    assert np.all(np.abs(got - ref) <= bound * (1 + 1e-9) + 1e-12)
+    assert np.abs(got - ref).max() > 0  # the approximation is not silently exact
