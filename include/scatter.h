@@ -379,6 +379,53 @@ typedef struct scatter_microbench_result {
 scatter_status scatter_microbench(int kind, int iters,
                                   scatter_microbench_result* result);
 
+/* ---- Eq. 5/6: the FFT approximation (Section 2.1) -------------------------
+ *
+ * Every atom is placed on the nearest node R_j of a triperiodic grid of step
+ * `step` (lattice units) starting at `origin`; with r_j = R_j + u_j the factor
+ * exp(2 i pi (S - H).u_j) is dropped, so that
+ *   A(H + q) ~ sum_s f_s(|S|) FT[ sum_{j in s} w_j exp(2 i pi H.r_j) ](q)
+ * is one discrete Fourier transform per species (cuFFT, loaded on first use).
+ * The output grid is S = H + q with q_d = (i_d - floor(n_d / 2)) / (n_d step),
+ * i_d in [0, n_d): index 0 holds the most negative q.  The approximation is
+ * valid while |(S - H).u_j| << 1 (Eq. 7); scatter_fft_validity reports that
+ * metric.  Atoms outside the grid are dropped and counted.                   */
+typedef struct scatter_fft_problem {
+  int64_t n_atoms;                 /* atoms per call                           */
+  int32_t n_species;               /* 1 .. 64                                  */
+  const scatter_species* species;  /* host [n_species]: f_s(|S|) (copied)      */
+  double lattice_a;                /* Angstrom                                 */
+  double center_hkl[3];            /* H, integers                              */
+  double step;                     /* grid step d, lattice units, > 0          */
+  double origin[3];                /* position of node (0, 0, 0), lattice units */
+  int64_t n[3];                    /* nodes per axis, 2 .. 4096                */
+} scatter_fft_problem;
+
+typedef struct scatter_fft_plan_s* scatter_fft_plan_t;
+
+/* Plans the grid (device memory n0 n1 n2 x n_species complex64 + cuFFT
+ * workspace).  SCATTER_ERR_UNSUPPORTED if cuFFT cannot be loaded or planned. */
+scatter_status scatter_fft_plan(const scatter_fft_problem* problem, scatter_fft_plan_t* out);
+
+/* A(S) on the plan's grid, device complex64 [n0][n1][n2] (A_out, caller-owned).
+ *   xyz          device FP64 [n_atoms][3], lattice units
+ *   atom_species device int32 [n_atoms] or NULL (all species 0); an index
+ *                outside [0, n_species) is counted and reported by
+ *                scatter_fft_validity
+ *   occ          device float [n_atoms] or NULL (all 1)
+ * Enqueued on `stream` (cudaStream_t); no device-wide synchronisation.      */
+scatter_status scatter_fft_amplitude(scatter_fft_plan_t plan, const double* xyz, const int32_t* atom_species,
+                                     const float* occ, void* A_out, void* stream);
+
+/* Eq. 7 metric of the last scatter_fft_amplitude call: max over atoms and
+ * over the output grid of |(S - H).u_j| (cycles), and the number of atoms
+ * that fell outside the grid.  Synchronises that call's stream.  Returns
+ * SCATTER_ERR_INVALID_ARG if an atom had a species index out of range.      */
+scatter_status scatter_fft_validity(scatter_fft_plan_t plan, double* max_qu, int64_t* n_outside);
+
+/* NULL-safe. */
+void scatter_fft_plan_destroy(scatter_fft_plan_t plan);
+
 #ifdef __cplusplus
 }  /* extern "C" */
 #endif

@@ -280,3 +280,61 @@ def microbench(kind: int, iters: int = 20000) -> dict:
     B.check(B.lib().scatter_microbench(int(kind), int(iters), ctypes.byref(r)), "scatter_microbench")
     return {"ops_per_s": r.ops_per_s, "ops_per_clk_per_sm": r.ops_per_clk_per_sm, "sm_clock_hz": r.sm_clock_hz,
             "seconds": r.seconds, "n_sm": r.n_sm}
+
+
+class FFTPlan:
+    """Eq. 5/6: the FFT approximation (scatter_fft_*).
+
+    Atoms go to the nearest node of a grid of `step` (lattice units) from
+    `origin` with `n` nodes per axis; A is returned on the grid
+    S = H + q, q_d = (i - n_d // 2) / (n_d step) (see axes()), valid while
+    |(S - H).u| << 1 (Eq. 7: validity()).
+    """
+
+    def __init__(self, coef, lattice_a: float, n_atoms: int, *, center, step: float, origin, n):
+        coef = np.asarray(coef, dtype=np.float64).reshape(-1, 12)
+        self._species = _species_array(coef)
+        pr = B.scatter_fft_problem()
+        pr.n_atoms = int(n_atoms)
+        pr.n_species = coef.shape[0]
+        pr.species = ctypes.addressof(self._species)
+        pr.lattice_a = float(lattice_a)
+        pr.center_hkl[:] = [float(c) for c in center]
+        pr.step = float(step)
+        pr.origin[:] = [float(o) for o in origin]
+        pr.n[:] = [int(k) for k in n]
+        self.center = np.asarray(center, dtype=np.float64)
+        self.step = float(step)
+        self.n = tuple(int(k) for k in n)
+        self.n_atoms = int(n_atoms)
+        h = ctypes.c_void_p()
+        B.check(B.lib().scatter_fft_plan(ctypes.byref(pr), ctypes.byref(h)), "scatter_fft_plan")
+        self._h = h
+
+    def axes(self):
+        """The three S axes of the output grid (r.l.u.)."""
+        return [self.center[d] + (np.arange(self.n[d]) - self.n[d] // 2) / (self.n[d] * self.step)
+                for d in range(3)]
+
+    def amplitude(self, xyz: torch.Tensor, atom_species: Optional[torch.Tensor] = None,
+                  occ: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        assert xyz.dtype == torch.float64 and xyz.is_cuda and xyz.is_contiguous() and xyz.shape[0] == self.n_atoms
+        sp = None if atom_species is None else atom_species.to(torch.int32).contiguous()
+        w = None if occ is None else occ.to(torch.float32).contiguous()
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.complex64, device=xyz.device)
+        B.check(B.lib().scatter_fft_amplitude(self._h, _ptr(xyz), _ptr(sp), _ptr(w), out.data_ptr(),
+                                              _stream(stream)), "scatter_fft_amplitude")
+        return out
+
+    def validity(self):
+        """(max over atoms and grid of |(S - H).u|, atoms outside the grid) of the last call."""
+        m, k = ctypes.c_double(), ctypes.c_int64()
+        B.check(B.lib().scatter_fft_validity(self._h, ctypes.byref(m), ctypes.byref(k)), "scatter_fft_validity")
+        return m.value, k.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            B.lib().scatter_fft_plan_destroy(h)
+            self._h = None

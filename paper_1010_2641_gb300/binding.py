@@ -81,6 +81,11 @@ class scatter_plan_info(ctypes.Structure):
                 ("center_hkl", c_double * 3), ("shift", c_double * 3), ("atoms_per_thread", c_int32)]
 
 
+class scatter_fft_problem(ctypes.Structure):
+    _fields_ = [("n_atoms", c_int64), ("n_species", c_int32), ("species", c_void_p), ("lattice_a", c_double),
+                ("center_hkl", c_double * 3), ("step", c_double), ("origin", c_double * 3), ("n", c_int64 * 3)]
+
+
 class scatter_microbench_result(ctypes.Structure):
     _fields_ = [("ops_per_s", c_double), ("ops_per_clk_per_sm", c_double), ("sm_clock_hz", c_double),
                 ("seconds", c_double), ("n_sm", c_int32)]
@@ -104,6 +109,10 @@ _PROTOTYPES = {
     "scatter_microbench": (c_int32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(scatter_microbench_result)]),
     "scatter_amplitude_noalloc": (c_int32, [c_int64, c_void_p, c_void_p, c_int64, c_void_p,
                                             ctypes.POINTER(c_double), c_void_p, c_void_p]),
+    "scatter_fft_plan": (c_int32, [ctypes.POINTER(scatter_fft_problem), ctypes.POINTER(c_void_p)]),
+    "scatter_fft_amplitude": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scatter_fft_validity": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
+    "scatter_fft_plan_destroy": (None, [c_void_p]),
 }
 
 _lib = None

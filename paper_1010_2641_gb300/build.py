@@ -28,6 +28,11 @@ NVCC_FLAGS = ARCH + [
 ]
 
 
+def _cuda_libdir(nvcc: str) -> str:
+    """The toolkit's library directory (fallback path for cuFFT, loaded at run time)."""
+    return str(pathlib.Path(nvcc).resolve().parents[1] / "lib64")
+
+
 def _nvcc() -> str:
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if cand and pathlib.Path(cand).exists():
@@ -48,7 +53,8 @@ def _stale() -> bool:
 
 
 def _compile(nvcc: str, src: pathlib.Path, obj: pathlib.Path) -> str:
-    cmd = [nvcc, *NVCC_FLAGS, "-I", str(INCLUDE), "-I", str(CSRC), "-c", str(src), "-o", str(obj)]
+    cmd = [nvcc, *NVCC_FLAGS, f'-DSCATTER_CUDA_LIBDIR="{_cuda_libdir(nvcc)}"', "-I", str(INCLUDE), "-I", str(CSRC),
+           "-c", str(src), "-o", str(obj)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src.name}:\n{r.stdout}\n{r.stderr}")

@@ -64,7 +64,7 @@ def test_struct_sizes_match_c_layout(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = [B.scatter_species, B.scatter_problem, B.scatter_options, B.scatter_plan_info,
-               B.scatter_microbench_result]
+               B.scatter_microbench_result, B.scatter_fft_problem]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "scatter.h"', "int main(void) {"]
     for st in structs:
         lines.append(f'  printf("%zu\\n", sizeof({st.__name__}));')
