@@ -409,10 +409,10 @@ def _tensor_roof(n0, n12, n_atoms_padded, ms):
             "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
 
 
-def measure_paths(args, dev, clk):
+def measure_paths(args, dev, clk, only=None):
     """The other rows of the hot path, each on its own workload (device time
     of the row's main kernel, CUDA events on the launching stream), each with
-    the roofline of its binding unit."""
+    the roofline of its binding unit.  `only`: run just the row(s) of that name."""
     import torch
     from paper_1010_2641_gb300 import api
     from paper_1010_2641_gb300 import workloads as W
@@ -420,108 +420,135 @@ def measure_paths(args, dev, clk):
     c, axes = workload()
     xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
     n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
-    # generic FP32/MUFU kernel on the full strained-sphere map, with its roofline
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     other = "generic" if args.path == "separable" else "separable"
-    plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, path=other, timing=True)
-    ms = _time_calls(lambda: plan.amplitude(xyz), plan)
-    row = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "workload": "strained sphere, full map"}
-    n_sm = plan.info()["n_sm"]
-    if other == "generic":
-        row["roofline"] = _rate_roof(n_atoms * n_s, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
-                                     "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")
-    else:
-        row["roofline"] = _tensor_roof(GRID[0], GRID[1] * GRID[2], plan.info()["n_atoms_padded"], ms)
-    res[f"{other}_sphere"] = row
-    del plan
-    # plain FP64 kernel on a 1/16 slice of the same map (every 16th l plane)
-    sub = [axes[0], axes[1], axes[2][::16]]
-    n_sub = len(sub[0]) * len(sub[1]) * len(sub[2])
-    plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=sub, atom_species=c.species, path="fp64", timing=True)
-    ms = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
-    res["fp64_sphere_slice"] = {"value": n_atoms * n_sub / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "n_s": n_sub}
-    del plan, xyz
-    # FFT approximation (Eq. 5/6) of the same crystal on a 256^3 grid of step 0.5 cells
-    # (S within +-1 r.l.u. of (004)), against the direct sum on that grid
-    xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
-    sp = torch.tensor(c.species, dtype=torch.int32, device=dev)
-    fp = api.FFTPlan(c.coef, W.LATTICE_A, n_atoms, center=(0, 0, 4), step=0.5,
-                     origin=np.floor(c.xyz.min(0)) - 1.0, n=(256, 256, 256))
-    A_fft = fp.amplitude(xyz, sp)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    torch.cuda.synchronize()
-    ev[0].record()
-    fp.amplitude(xyz, sp, out=A_fft)
-    ev[1].record()
-    torch.cuda.synchronize()
-    ms_fft = ev[0].elapsed_time(ev[1])
-    max_qu, outside = fp.validity()
-    plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=fp.axes(), atom_species=c.species, path="separable",
-                    timing=True)
-    ms_dir = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
-    A_dir = plan.amplitude(xyz).reshape(A_fft.shape)
-    err = (torch.linalg.vector_norm(A_fft - A_dir) / torch.linalg.vector_norm(A_dir)).item()
-    # the same near H: |q_d| <= 0.1 r.l.u. (12 bins of 1/128 r.l.u. each side), where |q.u| is 10x smaller
-    win = slice(128 - 12, 128 + 13)
-    a_w, d_w = A_fft[win, win, win], A_dir[win, win, win]
-    err_near = (torch.linalg.vector_norm(a_w - d_w) / torch.linalg.vector_norm(d_w)).item()
-    n_fft = 256 ** 3
-    res["fft_sphere_approx"] = {"value": n_atoms * n_fft / (ms_fft * 1e-3), "unit": UNIT + " (equivalent)",
-                                "call_ms": ms_fft, "direct_separable_ms": ms_dir, "rel_l2_vs_direct": err,
-                                "rel_l2_vs_direct_within_0.1_rlu": err_near,
-                                "eq7_max_qu_cycles": max_qu, "atoms_outside": outside,
-                                "workload": "strained sphere on a 256^3 grid of step 0.5 cells: deposit + cuFFT "
-                                            "(2 species) + f_s epilogue, against the separable direct sum"}
-    del plan, fp, A_fft, A_dir, xyz, sp
-    # adjoint on the strained cube (102,400 atoms x 128^3)
-    cube = W.strained_cube()
-    ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
-          W.linspace_axis(4.0, 128, step=0.005)]
-    plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, timing=True)
-    x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
-    I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
-    A = plan.amplitude(x)
-    ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
-    ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
-    res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
-                           "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr",
-                           # uniform l axis: the line kernel carries the phase along l by a complex multiply,
-                           # 8 FMA-pipe ops per pair at 128 lane-ops per SM per clock, no MUFU
-                           "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, clk, "Gpair/s", "alu",
-                                                  "pairs (8 FMA-pipe ops each)")}
-    del plan, x, A, I_obs
-    # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
-    isl = W.truncated_pyramid()
-    gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
-    plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
-                    gid=gid, timing=True)
-    x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
-    ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
-    m_gid = 512 * 512 * 32
-    res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
-                          "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel",
-                          # 16 FFMA per (atom, point) for the four beams: 8 points = 32 beam-pairs per SM per clock
-                          "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 32.0, n_sm, clk, "Gbeam-pair/s",
-                                                 "alu", "beam-pairs (16 FFMA per atom-point, 128 FFMA/SM/clk)")}
-    del plan
-    plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
-                    gid=gid, path="separable", timing=True)
-    ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
-    res["dwba_island_separable"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
-                                    "kernel_ms": ms,
-                                    "workload": "same map, beams stacked on a virtual l axis, tensor cores",
-                                    "roofline": _tensor_roof(512, 512 * 4 * 32, plan.info()["n_atoms_padded"], ms)}
-    del plan, x
-    # batched persistent launch, CUDA-graph replay (64 uneven crystals)
-    bx, bs, bcoef, bS, ao, so = W.ewald_batch()
-    plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True)
-    x = torch.tensor(bx, dtype=torch.float64, device=dev)
-    out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
-    ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
-    pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
-    res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
-                          "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
-                          "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
-                                                 "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
+
+    def want(name):
+        return only is None or only == name or (name == "dwba_island" and only.startswith("dwba_island"))
+
+    if want(f"{other}_sphere"):
+        # generic FP32/MUFU kernel on the full strained-sphere map, with its roofline
+        other = "generic" if args.path == "separable" else "separable"
+        plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, path=other, timing=True)
+        ms = _time_calls(lambda: plan.amplitude(xyz), plan)
+        row = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "workload": "strained sphere, full map"}
+        n_sm = plan.info()["n_sm"]
+        if other == "generic":
+            row["roofline"] = _rate_roof(n_atoms * n_s, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+                                         "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")
+        else:
+            row["roofline"] = _tensor_roof(GRID[0], GRID[1] * GRID[2], plan.info()["n_atoms_padded"], ms)
+        res[f"{other}_sphere"] = row
+        del plan
+    if want('fp64_sphere_slice'):
+        # plain FP64 kernel on a 1/16 slice of the same map (every 16th l plane)
+        sub = [axes[0], axes[1], axes[2][::16]]
+        n_sub = len(sub[0]) * len(sub[1]) * len(sub[2])
+        plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=sub, atom_species=c.species, path="fp64", timing=True)
+        ms = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
+        res["fp64_sphere_slice"] = {"value": n_atoms * n_sub / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "n_s": n_sub}
+        del plan, xyz
+    if want('fft_sphere_approx'):
+        # FFT approximation (Eq. 5/6) of the same crystal on a 256^3 grid of step 0.5 cells
+        # (S within +-1 r.l.u. of (004)), against the direct sum on that grid
+        xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
+        sp = torch.tensor(c.species, dtype=torch.int32, device=dev)
+        fp = api.FFTPlan(c.coef, W.LATTICE_A, n_atoms, center=(0, 0, 4), step=0.5,
+                         origin=np.floor(c.xyz.min(0)) - 1.0, n=(256, 256, 256))
+        A_fft = fp.amplitude(xyz, sp)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        fp.amplitude(xyz, sp, out=A_fft)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms_fft = ev[0].elapsed_time(ev[1])
+        max_qu, outside = fp.validity()
+        plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=fp.axes(), atom_species=c.species, path="separable",
+                        timing=True)
+        ms_dir = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
+        A_dir = plan.amplitude(xyz).reshape(A_fft.shape)
+        err = (torch.linalg.vector_norm(A_fft - A_dir) / torch.linalg.vector_norm(A_dir)).item()
+        # the same near H: |q_d| <= 0.1 r.l.u. (12 bins of 1/128 r.l.u. each side), where |q.u| is 10x smaller
+        win = slice(128 - 12, 128 + 13)
+        a_w, d_w = A_fft[win, win, win], A_dir[win, win, win]
+        err_near = (torch.linalg.vector_norm(a_w - d_w) / torch.linalg.vector_norm(d_w)).item()
+        n_fft = 256 ** 3
+        res["fft_sphere_approx"] = {"value": n_atoms * n_fft / (ms_fft * 1e-3), "unit": UNIT + " (equivalent)",
+                                    "call_ms": ms_fft, "direct_separable_ms": ms_dir, "rel_l2_vs_direct": err,
+                                    "rel_l2_vs_direct_within_0.1_rlu": err_near,
+                                    "eq7_max_qu_cycles": max_qu, "atoms_outside": outside,
+                                    "workload": "strained sphere on a 256^3 grid of step 0.5 cells: deposit + cuFFT "
+                                                "(2 species) + f_s epilogue, against the separable direct sum"}
+        del plan, fp, A_fft, A_dir, xyz, sp
+    if want('adjoint_cube'):
+        # adjoint on the strained cube (102,400 atoms x 128^3)
+        cube = W.strained_cube()
+        ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
+              W.linspace_axis(4.0, 128, step=0.005)]
+        plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, timing=True)
+        x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
+        I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
+        A = plan.amplitude(x)
+        ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
+        ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
+        res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                               "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr",
+                               # uniform l axis: the line kernel carries the phase along l by a complex multiply,
+                               # 8 FMA-pipe ops per pair at 128 lane-ops per SM per clock, no MUFU
+                               "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, clk, "Gpair/s", "alu",
+                                                      "pairs (8 FMA-pipe ops each)")}
+        del plan, x, A, I_obs
+    if want('dwba_island'):
+        # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
+        isl = W.truncated_pyramid()
+        gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
+        plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
+                        gid=gid, timing=True)
+        x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
+        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+        m_gid = 512 * 512 * 32
+        res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
+                              "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel",
+                              # 16 FFMA per (atom, point) for the four beams: 8 points = 32 beam-pairs per SM per clock
+                              "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 32.0, n_sm, clk, "Gbeam-pair/s",
+                                                     "alu", "beam-pairs (16 FFMA per atom-point, 128 FFMA/SM/clk)")}
+        del plan
+        plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
+                        gid=gid, path="separable", timing=True)
+        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+        res["dwba_island_separable"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
+                                        "kernel_ms": ms,
+                                        "workload": "same map, beams stacked on a virtual l axis, tensor cores",
+                                        "roofline": _tensor_roof(512, 512 * 4 * 32, plan.info()["n_atoms_padded"], ms)}
+        del plan, x
+    if want("atompar_few_reflections"):
+        # many atoms, few reflections: the atom-parallel form (the paper's speed test at 1e6 x 1e3)
+        rx, rS = W.random_sweep(1_000_000, 1000, seed=77)
+        plan = api.Plan(W.unit_species(), W.LATTICE_A, len(rx), s_list=rS, path="generic", timing=True)
+        x = torch.tensor(rx, dtype=torch.float64, device=dev)
+        out = torch.empty(len(rS), dtype=torch.complex64, device=dev)
+        ms = _time_calls(lambda: plan.amplitude(x, out=out), plan, reps=5)
+        pairs_a = float(len(rx) * len(rS))
+        res["atompar_few_reflections"] = {
+            "value": pairs_a / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+            "atoms_per_thread": plan.info()["atoms_per_thread"],
+            "workload": "1e6 random atoms x 1000 random reflections (atom-parallel form)",
+            "roofline": _rate_roof(pairs_a, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk, "Gpair/s",
+                                   "alu", "pairs (2 MUFU sin/cos each)")}
+        del plan, x, out
+    if want('batch_ewald'):
+        # batched persistent launch, CUDA-graph replay (64 uneven crystals)
+        bx, bs, bcoef, bS, ao, so = W.ewald_batch()
+        plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True)
+        x = torch.tensor(bx, dtype=torch.float64, device=dev)
+        out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
+        ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
+        pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
+        res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
+                              "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
+                              "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+                                                     "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
     return res
 
 
@@ -582,6 +609,7 @@ def main():
     ap.add_argument("--no-paths", action="store_true", help="skip the other rows' measurements")
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
     ap.add_argument("--sweep", default=None, help="speed sweep over atoms x reflections, e.g. 100,1000,10000")
+    ap.add_argument("--row", default=None, help="run one row of the paths section alone (profiling), e.g. adjoint_cube")
     ap.add_argument("--path", default="separable", choices=["generic", "separable"],
                     help="kernel family of the headline line (both meet the 1e-4 tolerance on this map)")
     args = ap.parse_args()
@@ -595,6 +623,11 @@ def main():
         return run_reference(args, rank, world)
     if args.sweep:
         return run_sweep(args)
+    if args.row:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"row": args.row, **measure_paths(args, "cuda:0", None, only=args.row)}))
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -13,7 +13,8 @@
 //                w e^{2 i pi H.r} into the species grid, Eq. 7 metric
 // cuFFT          one batched inverse C2C transform (exp(+2 i pi k.i/n))
 // k_fft_post     per output point (fftshifted order): f_s(|S|), the phase
-//                e^{2 i pi q.origin} of the grid origin, sum over species
+//                e^{2 i pi q.origin} of the grid origin (a product of three
+//                per-axis factors tabulated at plan time), sum over species
 //
 // cuFFT is loaded on first use (dlopen), so the rest of the library does not
 // depend on it; without it the calls return SCATTER_ERR_UNSUPPORTED.
@@ -36,6 +37,7 @@ struct scatter_fft_plan_s {
   bool have_fft = false;
   float2* grid = nullptr;       // [n_species][n_nodes]
   float* coef = nullptr;        // [n_species][12] FP32 form-factor coefficients
+  float2* ophase = nullptr;     // [n0 | n1 | n2] e^{2 i pi q_d o_d} per axis (the origin phase factorises)
   unsigned* stat = nullptr;     // [0] Eq. 7 metric (float bits), [1] atoms outside, [2] bad species
   cudaStream_t last_stream = nullptr;
 };
@@ -112,8 +114,8 @@ __global__ void k_fft_deposit(const double* __restrict__ xyz, const int32_t* __r
 }
 
 __global__ void k_fft_post(const float2* __restrict__ grid, int n_species, const float* __restrict__ coef,
-                           int64_t n0, int64_t n1, int64_t n2, double step, double H0, double H1, double H2,
-                           double o0, double o1, double o2, float inv4a2, float2* __restrict__ out) {
+                           int64_t n0, int64_t n1, int64_t n2, float dq0, float dq1, float dq2, float H0, float H1,
+                           float H2, const float2* __restrict__ ophase, float inv4a2, float2* __restrict__ out) {
   const int64_t n_nodes = n0 * n1 * n2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
@@ -122,15 +124,11 @@ __global__ void k_fft_post(const float2* __restrict__ grid, int n_species, const
   const int64_t k0 = i0 - n0 / 2, k1 = i1 - n1 / 2, k2 = i2 - n2 / 2;
   const int64_t b0 = k0 < 0 ? k0 + n0 : k0, b1 = k1 < 0 ? k1 + n1 : k1, b2 = k2 < 0 ? k2 + n2 : k2;
   const int64_t bin = (b0 * n1 + b1) * n2 + b2;
-  const double qx = (double)k0 / ((double)n0 * step), qy = (double)k1 / ((double)n1 * step),
-               qz = (double)k2 / ((double)n2 * step);
-  const double Sx = H0 + qx, Sy = H1 + qy, Sz = H2 + qz;
-  const float s2 = (float)(Sx * Sx + Sy * Sy + Sz * Sz) * inv4a2;
+  // |S| only enters the form factors: FP32 is ample (the FP64 pipe is slow)
+  const float Sx = fmaf((float)k0, dq0, H0), Sy = fmaf((float)k1, dq1, H1), Sz = fmaf((float)k2, dq2, H2);
+  const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * inv4a2;
   // the grid index i counts from `origin`: q.R = q.origin + k.i / n
-  double ph = qx * o0 + qy * o1 + qz * o2;
-  ph -= rint(ph);
-  double sn, cs;
-  sincospi(2.0 * ph, &sn, &cs);
+  const float2 e = dev::cmul(dev::cmul(ophase[i0], ophase[n0 + i1]), ophase[n0 + n1 + i2]);
   float2 v = make_float2(0.f, 0.f);
   for (int s = 0; s < n_species; ++s) {
     const float2 g = grid[(int64_t)s * n_nodes + bin];
@@ -139,7 +137,7 @@ __global__ void k_fft_post(const float2* __restrict__ grid, int n_species, const
     v.x += t.x;
     v.y += t.y;
   }
-  out[i] = dev::cmul(make_float2((float)cs, (float)sn), v);
+  out[i] = dev::cmul(e, v);
 }
 
 }  // namespace
@@ -197,6 +195,18 @@ scatter_status scatter_fft_plan(const scatter_fft_problem* pr, scatter_fft_plan_
   if ((e = cudaMemcpy(p->coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_status(e, "cudaMemcpy");
   if ((e = cudaMemset(p->stat, 0, 4 * sizeof(unsigned))) != cudaSuccess) return cuda_status(e, "cudaMemset");
+  // e^{2 i pi q_d o_d} for every output index of every axis, reduced mod 1 in FP64
+  std::vector<float2> oph;
+  for (int d = 0; d < 3; ++d)
+    for (int64_t i = 0; i < pr->n[d]; ++i) {
+      const double q = (double)(i - pr->n[d] / 2) / ((double)pr->n[d] * pr->step);
+      double ph = q * pr->origin[d];
+      ph -= std::rint(ph);
+      oph.push_back(make_float2((float)std::cos(2.0 * M_PI * ph), (float)std::sin(2.0 * M_PI * ph)));
+    }
+  if ((e = cudaMalloc(&p->ophase, oph.size() * sizeof(float2))) != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  if ((e = cudaMemcpy(p->ophase, oph.data(), oph.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_status(e, "cudaMemcpy");
   int dims[3] = {(int)pr->n[0], (int)pr->n[1], (int)pr->n[2]};
   if (api.plan_many(&p->fft, 3, dims, nullptr, 1, (int)p->n_nodes, nullptr, 1, (int)p->n_nodes, CUFFT_C2C,
                     pr->n_species) != CUFFT_SUCCESS)
@@ -237,9 +247,10 @@ scatter_status scatter_fft_amplitude(scatter_fft_plan_t p, const double* xyz, co
     return fail(SCATTER_ERR_CUDA, "cuFFT execution failed");
   }
   k_fft_post<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
-      p->grid, pr.n_species, p->coef, pr.n[0], pr.n[1], pr.n[2], pr.step, pr.center_hkl[0], pr.center_hkl[1],
-      pr.center_hkl[2], pr.origin[0], pr.origin[1], pr.origin[2],
-      (float)(1.0 / (4.0 * pr.lattice_a * pr.lattice_a)), static_cast<float2*>(A_out));
+      p->grid, pr.n_species, p->coef, pr.n[0], pr.n[1], pr.n[2], (float)(1.0 / ((double)pr.n[0] * pr.step)),
+      (float)(1.0 / ((double)pr.n[1] * pr.step)), (float)(1.0 / ((double)pr.n[2] * pr.step)), (float)pr.center_hkl[0],
+      (float)pr.center_hkl[1], (float)pr.center_hkl[2], p->ophase, (float)(1.0 / (4.0 * pr.lattice_a * pr.lattice_a)),
+      static_cast<float2*>(A_out));
   const scatter_status s = cuda_status(cudaGetLastError(), "FFT approximation launch");
   if (cur != p->device) cudaSetDevice(cur);
   return s;
@@ -266,6 +277,7 @@ void scatter_fft_plan_destroy(scatter_fft_plan_t p) {
   cudaFree(p->grid);
   cudaFree(p->coef);
   cudaFree(p->stat);
+  cudaFree(p->ophase);
   delete p;
 }
 
