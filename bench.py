@@ -537,6 +537,24 @@ def measure_paths(args, dev, clk, only=None):
             "roofline": _rate_roof(pairs_a, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk, "Gpair/s",
                                    "alu", "pairs (2 MUFU sin/cos each)")}
         del plan, x, out
+    if want("dwba_ge_dot"):
+        # the paper's germanium-dot example: (h, 0, alpha_f) map across (400), both DWBA paths
+        dot = W.ge_dot()
+        gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
+        ax = list(W.ge_dot_axes())
+        x = torch.tensor(dot.xyz, dtype=torch.float64, device=dev)
+        m_dot = len(ax[0]) * len(ax[1]) * len(ax[2])
+        row = {"unit": UNIT + " (x4 beams)", "workload": "Ge dot (669,753 atoms) x 512 h x 128 alpha_f across (400)"}
+        for name, pth in (("ffma", "generic"), ("separable", "separable")):
+            plan = api.Plan(dot.coef, W.LATTICE_A, len(dot.xyz), axes=ax, atom_species=dot.species, gid=gid,
+                            path=pth, timing=True)
+            ms = _time_calls(lambda: plan.amplitude(x), plan, reps=2)
+            row[f"{name}_ms"] = ms
+            row[f"{name}_value"] = 4 * len(dot.xyz) * m_dot / (ms * 1e-3)
+            del plan
+        row["value"] = max(row["ffma_value"], row["separable_value"])
+        res["dwba_ge_dot"] = row
+        del x
     if want('batch_ewald'):
         # batched persistent launch, CUDA-graph replay (64 uneven crystals)
         bx, bs, bcoef, bS, ao, so = W.ewald_batch()

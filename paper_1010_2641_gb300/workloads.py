@@ -314,3 +314,40 @@ def fcc_cell_blocks(n=(12, 12, 8), frac_type1: float = 0.3, amplitude: float = 0
     cell = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]], dtype=np.float64)
     return BlockModel(origins=cells + u, types=types, content=[cell, cell],
                       species=[np.zeros(4, np.int32), np.ones(4, np.int32)])
+
+
+def ge_dot(base_radius_cells: float = 50.0, height_cells: float = 20.0, seed: int = 6001) -> Crystal:
+    """The germanium quantum dot of the paper's grazing-incidence example
+    (Section 4.3): a spherical cap of base radius 50 cells and height 20
+    cells standing on the substrate (z >= 0), diamond lattice (8 atoms per
+    cell, Si/Ge), Ge fraction rising linearly from 0.2 at the bottom to 0.8
+    at the top (species drawn per atom, seeded), and the in-plane relaxation
+    eps_xx = eps_yy = 0.005 + z 0.002 (1 + sqrt(x^2 + y^2) / 50) of the
+    substrate lattice, applied as the dilation x -> x (1 + eps), y -> y (1 + eps)
+    (x, y, z fractional coordinates of the substrate lattice)."""
+    R, h = float(base_radius_cells), float(height_cells)
+    Rs = (R * R + h * h) / (2.0 * h)          # radius of the sphere the cap is cut from
+    zc = h - Rs                               # its centre (below the base plane)
+    n = int(np.ceil(R)) + 1
+    cells = np.stack(np.meshgrid(np.arange(-n, n + 1), np.arange(-n, n + 1), np.arange(0, int(np.ceil(h)) + 1),
+                                 indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    fcc = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    basis = np.concatenate([fcc, fcc + 0.25])                 # diamond
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    x, y, z = sites[:, 0], sites[:, 1], sites[:, 2]
+    keep = (z >= 0) & (z <= h) & (x * x + y * y + (z - zc) ** 2 <= Rs * Rs)
+    sites = sites[keep]
+    x, y, z = sites[:, 0], sites[:, 1], sites[:, 2]
+    eps = 0.005 + z * 0.002 * (1.0 + np.sqrt(x * x + y * y) / 50.0)
+    xyz = np.stack([x * (1.0 + eps), y * (1.0 + eps), z], 1)
+    rng = np.random.default_rng(seed)
+    ge = rng.uniform(size=len(xyz)) < 0.2 + 0.6 * z / h
+    return Crystal(xyz=xyz, species=ge.astype(np.int32), coef=si_ge_species())
+
+
+def ge_dot_axes(n_h: int = 512, n_af: int = 128):
+    """(h, k, alpha_f) axes of the dot's map: h across (400), k = 0, alpha_f in (0, 1 deg]."""
+    h = np.linspace(3.70, 4.10, n_h)
+    k = np.array([0.0])
+    af = np.deg2rad((np.arange(n_af) + 1) * (1.0 / n_af))
+    return h, k, af
