@@ -19,6 +19,17 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 // 16/clk/SM pipe on this GPU, the same rate as the MUFU sin/cos the kernels
 // are bound by, so it is avoided in the inner loops.)  The add/sub of
 // 1.5 * 2^23 rounds x to an integer in round-to-nearest-even.
+// Order-preserving map of doubles to unsigned integers (atomicMin/Max on
+// the bounding box) and its inverse.
+__device__ __forceinline__ unsigned long long ordered(double x) {
+  long long i = __double_as_longlong(x);
+  return (unsigned long long)(i >= 0 ? (i ^ (long long)0x8000000000000000ULL) : ~i);
+}
+__device__ __forceinline__ double unordered(unsigned long long u) {
+  long long i = (u & 0x8000000000000000ULL) ? (long long)(u ^ 0x8000000000000000ULL) : (long long)~u;
+  return __longlong_as_double(i);
+}
+
 __device__ __forceinline__ float frac_rn(float x) {
   const float kMagic = 12582912.0f;  // 1.5 * 2^23
   const float n = __fsub_rn(__fadd_rn(x, kMagic), kMagic);

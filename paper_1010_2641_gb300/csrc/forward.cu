@@ -30,14 +30,8 @@ namespace scatter {
 // prep
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ unsigned long long ordered(double x) {
-  long long i = __double_as_longlong(x);
-  return (unsigned long long)(i >= 0 ? (i ^ (long long)0x8000000000000000ULL) : ~i);
-}
-__device__ __forceinline__ double unordered(unsigned long long u) {
-  long long i = (u & 0x8000000000000000ULL) ? (long long)(u ^ 0x8000000000000000ULL) : (long long)~u;
-  return __longlong_as_double(i);
-}
+using dev::ordered;
+using dev::unordered;
 
 __global__ void k_bbox_init(unsigned long long* bbox, int batch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -175,6 +175,7 @@ struct scatter_plan_s {
   int64_t sep_n[3] = {0, 0, 0};                  // separable grid shape (GID: n_h, n_k, 4 n_af)
   int64_t sep_ns = 0;
   int32_t sep_n_chunks = 0;
+  float sep_smax[2] = {0.f, 0.f};               // max |s| of the separable grid's b and c axes
   int32_t ap_n_blocks = 0;
   std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
   bool adj_ready = false;

@@ -43,6 +43,7 @@
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 #include "device_common.cuh"
 #include "launch.h"
@@ -64,6 +65,7 @@ constexpr int kSepBStages = 2;             // B ring: formation of step k+1 over
 constexpr int kSepTStages = 8;             // atom-record ring (256 B per step)
 constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
 constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
+constexpr double kSepPhaseLim = 16.0;      // cycles: B phases below this skip the mod-1 reduction
 
 // -------------------------------------------------------------------------
 // descriptors (PTX tcgen05 shared-memory and instruction descriptors)
@@ -182,6 +184,9 @@ struct SepArgs {
   const float4* atom4;    // per slot (x', y', z', c)
   const Segment* chunks;  // per blockIdx.y: one species, slots a multiple of 16
   const float* axis_s;
+  const unsigned long long* bbox;  // instance 0: ordered min xyz, max xyz of this call's positions
+  const double* shift;             // instance 0: its centring t
+  float smax_b, smax_c;            // max |s| of the b and c axes
   int64_t n0, n1, n2, n_s;
   int64_t n_slots, n_steps, n_mt, n_nt;
   float* partial;   // [chunk][2][n_s] planar (re plane, im plane), T without f_s
@@ -355,6 +360,19 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
     const float sb = a.axis_s[a.n0 + rb], sc = a.axis_s[a.n0 + a.n1 + rc];
     const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+    // |s_b y' + s_c z' + c| of every B element of this call stays below
+    // kSepPhaseLim cycles when the centred extent is small: the exact mod-1
+    // reduction is then skipped (MUFU sin/cos of an argument of L cycles errs
+    // by ~L 2^-24 cycles, 6e-6 rad at the limit, below this path's 1e-4)
+    bool reduce = true;
+    {
+      const unsigned long long ylo = a.bbox[1], zlo = a.bbox[2], yhi = a.bbox[4], zhi = a.bbox[5];
+      if (ylo != ~0ULL && zlo != ~0ULL && yhi != 0ULL && zhi != 0ULL) {
+        const double ey = fmax(fabs(dev::unordered(ylo) - a.shift[1]), fabs(dev::unordered(yhi) - a.shift[1]));
+        const double ez = fmax(fabs(dev::unordered(zlo) - a.shift[2]), fabs(dev::unordered(zhi) - a.shift[2]));
+        reduce = (double)a.smax_b * (ey + 1.0) + (double)a.smax_c * (ez + 1.0) + 0.5 > kSepPhaseLim;
+      }
+    }
     float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
     float* part_im = part_re + a.n_s;
     bool first_flush = true;
@@ -375,22 +393,30 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       // B[(b,c), j] = e^{2 pi i (s_b y'_j + s_c z'_j + c_j)}, zero past the last point
       unsigned char* sB = ringB + bst * kSepBBytes;
       const float4* at = ring_atom[tst];
+      auto form = [&](auto reduce_tag) {
+        constexpr bool kReduce = decltype(reduce_tag)::value;
 #pragma unroll
-      for (int kb = 0; kb < 4; ++kb) {
-        uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
-        if (row_ok) {
+        for (int kb = 0; kb < 4; ++kb) {
+          uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
+          if (row_ok) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 v = at[kb * 4 + q];
-            const float ph = dev::frac_rn(fmaf(sb, v.y, fmaf(sc, v.z, v.w)));
-            float sn, cs;
-            dev::sincos_cycles_mufu(ph, &sn, &cs);
-            split2(cs, sn, hi[q], lo[q]);
+            for (int q = 0; q < 4; ++q) {
+              const float4 v = at[kb * 4 + q];
+              const float p = fmaf(sb, v.y, fmaf(sc, v.z, v.w));
+              const float ph = kReduce ? dev::frac_rn(p) : p;
+              float sn, cs;
+              dev::sincos_cycles_mufu(ph, &sn, &cs);
+              split2(cs, sn, hi[q], lo[q]);
+            }
           }
+          *reinterpret_cast<uint4*>(sB + kb * 4096 + b_row_off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        *reinterpret_cast<uint4*>(sB + kb * 4096 + b_row_off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
+      };
+      if (reduce)
+        form(std::true_type{});
+      else
+        form(std::false_type{});
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -572,6 +598,11 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     }
   }
   p->sep_ns = p->sep_n[0] * p->sep_n[1] * p->sep_n[2];
+  p->sep_smax[0] = p->sep_smax[1] = 0.f;
+  for (int64_t i = 0; i < p->sep_n[1]; ++i)
+    p->sep_smax[0] = std::max(p->sep_smax[0], std::fabs(alls[p->sep_n[0] + i]));
+  for (int64_t i = 0; i < p->sep_n[2]; ++i)
+    p->sep_smax[1] = std::max(p->sep_smax[1], std::fabs(alls[p->sep_n[0] + p->sep_n[1] + i]));
   const int64_t n_steps = p->n_slots / kSepStep;
   const int64_t n_mt = (2 * p->sep_n[0] + kSepM - 1) / kSepM;
   const int64_t n_nt = (p->sep_n[1] * p->sep_n[2] + kSepN - 1) / kSepN;
@@ -654,6 +685,10 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.A = static_cast<const uint4*>(p->d.sep_A);
   a.atom4 = p->d.atom4;
   a.chunks = p->d.sep_chunks;
+  a.bbox = p->d.inst_bbox;
+  a.shift = p->d.inst_shift;
+  a.smax_b = p->sep_smax[0];
+  a.smax_c = p->sep_smax[1];
   a.axis_s = p->d.sep_axis_s;
   a.n0 = p->sep_n[0];
   a.n1 = p->sep_n[1];

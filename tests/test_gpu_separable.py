@@ -100,3 +100,16 @@ def test_strained_sphere_full_size_sampled():
     idx[:8] = np.argsort(np.abs(A))[-8:]
     ref = oracle.amplitude(c.xyz, W.grid_points(axes)[idx], c.coef, A_LAT, species=c.species)
     assert rel_l2(A[idx], ref) < TOL_TC
+
+
+def test_wide_grid_takes_the_reduced_phase_path():
+    """A k axis spanning +-3 r.l.u. over a crystal of radius 8.5 cells puts
+    |s_b y'| near 27 cycles, above the limit under which B phases skip the
+    exact mod-1 reduction: this map exercises the reduced branch."""
+    c = W.fcc_sphere(radius_cells=8.5, shell_cells=2.0, seed=71)
+    axes = [np.linspace(-0.05, 0.05, 5), np.linspace(-3.0, 3.0, 61), np.linspace(3.9, 4.1, 17)]
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="separable")
+    A = plan.amplitude(torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0")).cpu().numpy().reshape(-1)
+    plan.check()
+    ref = oracle.amplitude(c.xyz, W.grid_points(axes), c.coef, A_LAT, species=c.species)
+    assert rel_l2(A, ref) < 1e-4
