@@ -166,7 +166,7 @@ def kernel_source_hash(files=GENERIC_SOURCES) -> str:
     return h.hexdigest()[:12]
 
 
-SEP_SOURCES = ("separable.cu", "device_common.cuh", "plan.h")
+SEP_SOURCES = ("separable.cu", "sep_common.cuh", "device_common.cuh", "plan.h")
 
 
 def profiled_traffic(name="generic_strained_sphere.md", files=GENERIC_SOURCES):
@@ -415,6 +415,34 @@ def _tensor_roof(n0, n12, n_atoms_padded, ms):
             "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
 
 
+def _tensor_roof_adjoint(n0, n12, n_atoms_padded, ms):
+    """Executed-flop roofline of k_sep running the adjoint: rows (a, weight,
+    Re/Im) = 6 n0, columns = atom slots in 256-slot tiles, K = 2 per point."""
+    m_pad = -(-6 * n0 // 128) * 128
+    n_pad = -(-n_atoms_padded // 256) * 256
+    k_pad = -(-n12 // 16) * 16 * 2
+    executed = 6.0 * m_pad * n_pad * k_pad
+    peak, basis = measured_peak("bf16_tflops", 1900.0)
+    achieved = executed / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+
+
+def _time_whole(fn, reps=3):
+    """Device time of whole calls (every kernel they launch), CUDA events on
+    torch's current stream, where the plan launches."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        fn()
+    t1.record()
+    t1.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
 def measure_paths(args, dev, clk, only=None):
     """The other rows of the hot path, each on its own workload (device time
     of the row's main kernel, CUDA events on the launching stream), each with
@@ -504,6 +532,25 @@ def measure_paths(args, dev, clk, only=None):
                                # 8 FMA-pipe ops per pair at 128 lane-ops per SM per clock, no MUFU
                                "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, clk, "Gpair/s", "alu",
                                                       "pairs (8 FMA-pipe ops each)")}
+        del plan, x, A, I_obs
+    if want('adjoint_cube_separable'):
+        # the same gradient on a SEPARABLE plan: the per-atom sums contract on the tensor cores
+        cube = W.strained_cube()
+        ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
+              W.linspace_axis(4.0, 128, step=0.005)]
+        plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, path="separable", timing=True)
+        x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
+        I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
+        A = plan.amplitude(x)
+        ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
+        ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
+        ms_call = _time_whole(lambda: plan.backward(x, A, I_obs))
+        assert plan.info()["adjoint_form"] == 3
+        res["adjoint_cube_separable"] = {
+            "value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "call_ms": ms_call,
+            "call_value": len(cube.xyz) * 128 ** 3 / (ms_call * 1e-3), "forward_kernel_ms": ms_f,
+            "workload": "strained cube 102400 atoms x 128^3, dL/dr on a SEPARABLE plan (k_sep, operands swapped)",
+            "roofline": _tensor_roof_adjoint(128, 128 * 128, plan.info()["n_atoms_padded"], ms)}
         del plan, x, A, I_obs
     if want('dwba_island'):
         # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)

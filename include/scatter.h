@@ -179,6 +179,11 @@ typedef struct scatter_plan_info {
   double center_hkl[3];      /* H of instance 0                                */
   double shift[3];           /* integer centring vector t of instance 0        */
   int32_t atoms_per_thread;  /* > 0: the atom-parallel form was chosen        */
+  int32_t adjoint_form;      /* form of the gradient kernel, fixed at the first
+                              * backward: 0 none yet, 1 FP32 S tiles (lists,
+                              * non-uniform grids), 2 FP32 line recurrence
+                              * (uniform l axis), 3 tensor-core contraction
+                              * (SEPARABLE grid plans)                         */
 } scatter_plan_info;
 
 /* ------------------------------------------------------------------------ */
@@ -245,6 +250,13 @@ scatter_status scatter_intensity(scatter_plan_t plan, const double* xyz,
  *  loss_out   device float64 scalar, or NULL.
  *  dL_dxyz    device float32 [n_atoms][3] in the caller's atom order, or NULL.
  *
+ * Kernel form: on a SEPARABLE plan of one GRID the per-atom sums over S
+ * factorise like the forward and run as a complex contraction on the tensor
+ * cores (split-f16 products, FP32 accumulation, FP64 sum over the first
+ * axis; gradient error of the split path's 1e-3 class), unless its workspace
+ * (about 56 B per point and species plus 24 n0 B per atom) would exceed
+ * 32 GiB; every other plan runs FP32 atom-parallel kernels
+ * (scatter_plan_info.adjoint_form says which).
  * Not available for GID_GRID plans (UNSUPPORTED).
  */
 scatter_status scatter_backward(scatter_plan_t plan, const double* xyz,

@@ -78,7 +78,8 @@ class scatter_options(ctypes.Structure):
 class scatter_plan_info(ctypes.Structure):
     _fields_ = [("path", c_int32), ("threads", c_int32), ("points_per_thread", c_int32), ("split_k", c_int32),
                 ("n_sm", c_int32), ("n_atoms_padded", c_int64), ("n_s", c_int64), ("workspace_bytes", c_int64),
-                ("center_hkl", c_double * 3), ("shift", c_double * 3), ("atoms_per_thread", c_int32)]
+                ("center_hkl", c_double * 3), ("shift", c_double * 3), ("atoms_per_thread", c_int32),
+                ("adjoint_form", c_int32)]
 
 
 class scatter_fft_problem(ctypes.Structure):

@@ -48,8 +48,10 @@ struct LossArgs {
   const float* coef;
   int n_species;
   float inv4a2;
-  int line;               // 1: compact rows (s_z, S_z, gF.re, gF.im) for k_adjoint_line
-  float4* table;          // [n_species][M][2], or [n_species][M] (line)
+  int layout;             // 0: rows {s, gF.re | S, gF.im} for k_adjoint; 1: compact rows
+                          // (s_z, S_z, gF.re, gF.im) for k_adjoint_line; 2: gF alone (adjoint_sep.cu)
+  float4* table;          // [n_species][M][2] (layout 0), [n_species][M] (layout 1)
+  float2* gf;             // [n_species][M] (layout 2)
   double* loss_part;      // [gridDim.x]
 };
 
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a)
     const float sx = (float)(S[0] - a.H[0]), sy = (float)(S[1] - a.H[1]), sz = (float)(S[2] - a.H[2]);
     for (int sp = 0; sp < a.n_species; ++sp) {
       const float2 gF = dev::cmul(gp, dev::form_factor(a.coef + kNCoef * sp, s2));
-      if (a.line) {
+      if (a.layout == 2) {
+        a.gf[(int64_t)sp * a.n_s + m] = gF;
+      } else if (a.layout == 1) {
         a.table[(int64_t)sp * a.n_s + m] = make_float4(sz, Sz, gF.x, gF.y);
       } else {
         float4* row = a.table + 2 * ((int64_t)sp * a.n_s + m);
@@ -395,6 +399,13 @@ __global__ void k_adjoint_final(const float* partial, int split, int64_t n_slots
 scatter_status prepare_adjoint(scatter_plan_s* p) {
   if (p->adj_ready) return SCATTER_OK;
   if (p->batch != 1) return fail(SCATTER_ERR_UNSUPPORTED, "backward is available for single instances");
+  // a SEPARABLE grid plan contracts on the tensor cores when its workspace fits
+  scatter_status ss = prepare_adjoint_sep(p);
+  if (ss != SCATTER_OK) return ss;
+  if (p->adj_sep) {
+    p->adj_ready = true;
+    return SCATTER_OK;
+  }
   std::vector<AdjBlock> blocks;
   const int per = kAdjThreads * kAdjRA;
   for (const Segment& s : p->all_segs)
@@ -503,8 +514,9 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
   la.coef = p->d.coef;
   la.n_species = grad ? p->n_species : 0;
   la.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
-  la.line = grad && p->adj_line;
+  la.layout = !grad ? 0 : (p->adj_sep ? 2 : (p->adj_line ? 1 : 0));
   la.table = p->d.adj_table;
+  la.gf = p->d.adj_gf;
   la.loss_part = p->d.loss_part;
   k_loss_weights<<<kLossParts, kLossThreads, 0, st>>>(la);
   p->last_launches += 1;
@@ -512,6 +524,7 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
     k_loss_final<<<1, 32, 0, st>>>(p->d.loss_part, kLossParts, loss_out);
     p->last_launches += 1;
   }
+  if (grad && p->n_atoms > 0 && p->adj_sep) return launch_adjoint_sep(p, grad, st);
   if (grad && p->n_atoms > 0) {
     AdjArgs aa{};
     aa.atom4 = p->d.atom4;

@@ -178,6 +178,7 @@ extern "C" scatter_status scatter_plan_get_info(scatter_plan_t p, scatter_plan_i
   info->points_per_thread = p->tiling.R;
   info->split_k = p->tiling.split_k;
   info->atoms_per_thread = p->tiling.atom_k;
+  info->adjoint_form = !p->adj_ready ? 0 : (p->adj_sep ? 3 : (p->adj_line ? 2 : 1));
   info->n_sm = p->n_sm;
   info->n_atoms_padded = p->n_slots;
   info->n_s = p->n_s;

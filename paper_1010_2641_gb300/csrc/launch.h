@@ -36,6 +36,11 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
                                const float* I_obs, const float2* G, double* loss_out, float* grad,
                                cudaStream_t st);
 
+// Tensor-core adjoint on grids of SEPARABLE plans (adjoint_sep.cu).
+bool adjoint_sep_applicable(const scatter_plan_s* p);
+scatter_status prepare_adjoint_sep(scatter_plan_s* p);
+scatter_status launch_adjoint_sep(scatter_plan_t p, float* grad, cudaStream_t st);
+
 // Grazing-incidence (DWBA) path: plan tables, split choice, launches.
 scatter_status prepare_gid(scatter_plan_s* p);
 int dwba_best_split(const scatter_plan_s* p);

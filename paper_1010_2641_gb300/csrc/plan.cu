@@ -258,6 +258,13 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.adj_blocks);
   release(d.adj_table);
   release(d.adj_partial);
+  release(d.adj_gf);
+  release(d.adj_sexp);
+  release(d.adj_sepA);
+  release(d.adj_sep_partial);
+  release(d.adj_rec);
+  release(d.adj_ntiles);
+  release(d.adj_kchunks);
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);
   if (p->ev_end) cudaEventDestroy(p->ev_end);
   if (prev >= 0) cudaSetDevice(prev);

@@ -128,6 +128,14 @@ struct DeviceBuffers {
   AdjBlock* adj_blocks = nullptr;
   float4* adj_table = nullptr;      // [n_species][M][2], or [n_species][M] in line mode
   float* adj_partial = nullptr;     // [split][n_slots][3]
+  // tensor-core adjoint on grids (adjoint_sep.cu)
+  float2* adj_gf = nullptr;         // [n_species][M] gF_s
+  int* adj_sexp = nullptr;          // [n_species][3][n0] row scale exponents
+  void* adj_sepA = nullptr;         // A blocks [species][M-tile pair][point step][2][hi|lo]
+  float* adj_sep_partial = nullptr; // [chunk][Re, Im][3 n0][n_slots]
+  float4* adj_rec = nullptr;        // point records (0, s_b, s_c, 0), 16 per step
+  Segment* adj_ntiles = nullptr;    // 256-slot atom tiles of one species
+  Segment* adj_kchunks = nullptr;   // point-step chunks (split over K)
 };
 
 }  // namespace scatter
@@ -185,4 +193,8 @@ struct scatter_plan_s {
   bool adj_line = false;            // uniform-l grid: k_adjoint_line (phase recurrence)
   float adj_ds = 0.f;               // its l step
   int64_t adj_lines_per_chunk = 0;
+  bool adj_sep = false;             // SEPARABLE grid plan: the adjoint runs on k_sep
+  int64_t adj_sep_ksteps = 0, adj_sep_mt = 0;
+  int32_t adj_sep_ntiles = 0, adj_sep_chunks = 0;
+  float adj_sep_smax[2] = {0.f, 0.f};
 };

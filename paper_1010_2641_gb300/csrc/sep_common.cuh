@@ -1,0 +1,116 @@
+// Shared pieces of the tcgen05 contraction kernel k_sep: tile constants,
+// descriptors, the MMA / TMEM wrappers, the f16 hi/lo split and the kernel
+// arguments.  k_sep computes, for one CTA, D[rows, cols] = sum_K A[rows, K]
+// B[cols, K] with A read as precomputed f16 hi/lo blocks and B formed in
+// the kernel: B[col, (k, Re|Im)] = e^{2 pi i (u_col v_k + w_col z_k + c_k)}
+// from a per-column pair (u, w) and a per-K record (., v, z, c).
+//   forward (Eq. 2):  cols = grid points (s_b, s_c), K = atoms (y', z', c)
+//   adjoint:          cols = atoms (y', z'),        K = grid points (s_b, s_c, 0)
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "device_common.cuh"
+#include "plan.h"
+
+namespace scatter {
+
+constexpr int kSepFormWarps = 8;           // warps forming B rows (one N column per thread)
+constexpr int kSepThreads = 32 * (kSepFormWarps + 2);  // + the MMA warp + the copy warp
+constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
+constexpr int kSepN = 256;                 // MMA N (columns per CTA)
+constexpr int kSepStep = 16;               // K records per pipeline step (K' = 32)
+constexpr int kSepFlush = 256;             // steps between TMEM flushes
+constexpr uint32_t kSepABytes = 16384;     // A block of one M tile: hi + lo, 128 x 32 f16 each
+constexpr int kSepPair = 2;                // M tiles per CTA (one formed B tile feeds both)
+constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
+constexpr int kSepAStages = 4;             // A ring (full / empty barrier per stage)
+constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
+constexpr int kSepTStages = 8;             // K-record ring (256 B per step)
+constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
+constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
+constexpr double kSepPhaseLim = 16.0;      // cycles: B phases below this skip the mod-1 reduction
+
+// -------------------------------------------------------------------------
+// descriptors (PTX tcgen05 shared-memory and instruction descriptors)
+// -------------------------------------------------------------------------
+
+// No-swizzle K-major operand: 8-row x 16-byte core matrices; lbo = byte
+// stride between core matrices along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor core
+  return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// kind::f16: D f32, A and B f16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kSepIdesc = (1u << 4) | ((uint32_t)(kSepN >> 3) << 17) | ((uint32_t)(kSepM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kSepIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   dev::smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// f16 hi/lo split of two floats packed as f16x2 each.
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(y), "f"(x));
+  const __half2 h = *reinterpret_cast<const __half2*>(&hi);
+  const float2 hf = __half22float2(h);
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - hf.y), "f"(x - hf.x));
+}
+
+struct SepArgs {
+  const uint4* A;         // A blocks [species][M-tile pair][step][2 tiles][hi|lo] of 16 KB per tile
+  int64_t a_sp_stride;    // uint4 per species table of A (0: one table, the forward)
+  const float4* rec;      // K records, 16 per step: forward the atom slots (x', y', z', c),
+                          // adjoint the grid points (0, s_b, s_c, 0)
+  const Segment* chunks;  // per blockIdx.y: K range in records (multiples of 16)
+  const Segment* ntiles;  // adjoint: slot range and species of each N tile; null: N = grid points
+  const float4* atom4;    // adjoint: the columns' atoms (y', z' read)
+  const float* axis_s;    // forward: the columns' points, s = axis - H ([n0 | n1 | n2])
+  const unsigned long long* bbox;  // instance 0: ordered min xyz, max xyz of this call's positions
+  const double* shift;             // instance 0: its centring t
+  float smax_b, smax_c;            // max |s| of the b and c axes
+  int64_t n0, n1, n2;     // grid shape
+  int64_t n_rows;         // rows of each partial plane (forward n0, adjoint 3 n0)
+  int64_t ld;             // floats between rows of a plane (forward n1 n2, adjoint n_slots)
+  int64_t plane;          // floats per plane
+  int64_t n_steps, n_mt;  // K steps per A table, M tiles
+  float* partial;         // [chunk][Re, Im][n_rows][ld] planar, raw D (no f_s)
+  unsigned* status;
+};
+
+// Launches k_sep on `st` (its shared-memory attribute set by sep_prepare_kernel).
+cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st);
+cudaError_t sep_prepare_kernel();
+
+}  // namespace scatter

@@ -39,89 +39,17 @@
 // tensor core's FP32 accumulation error down); k_sep_reduce sums the chunks
 // in order, each times its species' f_s(|S|), and applies the translation
 // phase.
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
+// The same kernel, with the roles of the operands swapped, runs the adjoint
+// on grids (adjoint_sep.cu); the arguments in sep_common.cuh cover both.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
-#include "device_common.cuh"
 #include "launch.h"
+#include "sep_common.cuh"
 #include "tuner.h"
 
 namespace scatter {
-
-constexpr int kSepFormWarps = 8;           // warps forming B rows (one point per thread)
-constexpr int kSepThreads = 32 * (kSepFormWarps + 2);  // + the MMA warp + the copy warp
-constexpr int kSepM = 128;                 // MMA M (rows of A per CTA)
-constexpr int kSepN = 256;                 // MMA N (points per CTA)
-constexpr int kSepStep = 16;               // atoms per pipeline step (K' = 32)
-constexpr int kSepFlush = 256;             // steps between TMEM flushes
-constexpr uint32_t kSepABytes = 16384;     // A block of one M tile: hi + lo, 128 x 32 f16 each
-constexpr int kSepPair = 2;                // M tiles per CTA (one formed B tile feeds both)
-constexpr uint32_t kSepBBytes = 32768;     // B block: hi + lo, 256 x 32 f16 each
-constexpr int kSepAStages = 4;             // A ring (full / empty barrier per stage)
-constexpr int kSepBStages = 2;             // B ring: formation of step k+1 overlaps MMAs of k
-constexpr int kSepTStages = 8;             // atom-record ring (256 B per step)
-constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
-constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
-constexpr double kSepPhaseLim = 16.0;      // cycles: B phases below this skip the mod-1 reduction
-
-// -------------------------------------------------------------------------
-// descriptors (PTX tcgen05 shared-memory and instruction descriptors)
-// -------------------------------------------------------------------------
-
-// No-swizzle K-major operand: 8-row x 16-byte core matrices; lbo = byte
-// stride between core matrices along K, sbo = along M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor core
-  return d;                // base offset 0, layout type 0 (no swizzle)
-}
-
-// kind::f16: D f32, A and B f16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kSepIdesc = (1u << 4) | ((uint32_t)(kSepN >> 3) << 17) | ((uint32_t)(kSepM >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kSepIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   dev::smem_addr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
-      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// f16 hi/lo split of two floats packed as f16x2 each.
-__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(y), "f"(x));
-  const __half2 h = *reinterpret_cast<const __half2*>(&hi);
-  const float2 hf = __half22float2(h);
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - hf.y), "f"(x - hf.x));
-}
 
 // -------------------------------------------------------------------------
 // tables
@@ -179,19 +107,6 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
 // main kernel
 // -------------------------------------------------------------------------
 
-struct SepArgs {
-  const uint4* A;
-  const float4* atom4;    // per slot (x', y', z', c)
-  const Segment* chunks;  // per blockIdx.y: one species, slots a multiple of 16
-  const float* axis_s;
-  const unsigned long long* bbox;  // instance 0: ordered min xyz, max xyz of this call's positions
-  const double* shift;             // instance 0: its centring t
-  float smax_b, smax_c;            // max |s| of the b and c axes
-  int64_t n0, n1, n2, n_s;
-  int64_t n_slots, n_steps, n_mt, n_nt;
-  float* partial;   // [chunk][2][n_s] planar (re plane, im plane), T without f_s
-  unsigned* status;
-};
 
 // Accumulation groups: the steps between two TMEM flushes (every kSepFlush
 // steps and at the end of the chunk).  Both roles walk them identically.
@@ -241,6 +156,15 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   const int ntp = 2 * mp + 1 < a.n_mt ? 2 : 1;  // M tiles of this CTA with rows
   const int chunk = blockIdx.y;
   const int64_t nbc = a.n1 * a.n2;
+  // this CTA's columns [col_base, col_end) and the species of its A table
+  int64_t col_base = nt * kSepN, col_end = nbc;
+  int a_species = 0;
+  if (a.ntiles) {
+    const Segment t = a.ntiles[nt];
+    col_base = t.begin;
+    col_end = t.end;
+    a_species = t.species;
+  }
 
   if (mma_warp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dev::smem_addr(&tmem_slot)),
@@ -268,7 +192,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // the chunk's steps: one species, slot bounds on step edges
+  // the chunk's steps (record bounds on step edges)
   const int64_t ks_begin = a.chunks[chunk].begin / kSepStep, ks_end = a.chunks[chunk].end / kSepStep;
   SepGroups grp{ks_end, ks_begin};
   bool ok = true;
@@ -277,9 +201,9 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 
   if (copy_warp) {
     if (lane == 0) {
-      // A block and atom records of every step, in step order; a stage is
+      // A block and K records of every step, in step order; a stage is
       // refilled once its previous contents were consumed
-      const uint4* Ablk = a.A + mp * a.n_steps * (kSepPair * kSepABytes / 16);
+      const uint4* Ablk = a.A + a_species * a.a_sp_stride + mp * a.n_steps * (kSepPair * kSepABytes / 16);
       const uint32_t a_bytes = (uint32_t)ntp * kSepABytes;
       int64_t g = 0;
       for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -294,7 +218,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           break;
         }
         dev::mbar_arrive_expect_tx(&bar_atom[tst], kSepStep * sizeof(float4));
-        dev::bulk_g2s(&ring_atom[tst][0], a.atom4 + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
+        dev::bulk_g2s(&ring_atom[tst][0], a.rec + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
         t_issued = g + 1;
         if (g >= kSepAStages &&
             !dev::mbar_wait_bounded(&bar_done[ast], (uint32_t)(((g - kSepAStages) / kSepAStages) & 1))) {
@@ -354,11 +278,20 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     }
   } else {
     // ---- formation warps ---------------------------------------------------
-    // this thread's B row: point bc of the N tile, offsets (s_b, s_c) from H
-    const int64_t bc = nt * kSepN + tid;
-    const bool row_ok = bc < nbc;
-    const int64_t rb = row_ok ? bc / a.n2 : 0, rc = row_ok ? bc % a.n2 : 0;
-    const float sb = a.axis_s[a.n0 + rb], sc = a.axis_s[a.n0 + a.n1 + rc];
+    // this thread's B row (column col of D): forward the point (b, c) with
+    // offsets (s_b, s_c) from H, adjoint the atom's (y', z')
+    const int64_t col = col_base + tid;
+    const bool row_ok = col < col_end;
+    float sb, sc;
+    if (a.ntiles) {
+      const float4 at = row_ok ? a.atom4[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sb = at.y;
+      sc = at.z;
+    } else {
+      const int64_t rb = row_ok ? col / a.n2 : 0, rc = row_ok ? col % a.n2 : 0;
+      sb = a.axis_s[a.n0 + rb];
+      sc = a.axis_s[a.n0 + a.n1 + rc];
+    }
     const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
     // |s_b y' + s_c z' + c| of every B element of this call stays below
     // kSepPhaseLim cycles when the centred extent is small: the exact mod-1
@@ -373,8 +306,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         reduce = (double)a.smax_b * (ey + 1.0) + (double)a.smax_c * (ez + 1.0) + 0.5 > kSepPhaseLim;
       }
     }
-    float* part_re = a.partial + (int64_t)chunk * 2 * a.n_s;
-    float* part_im = part_re + a.n_s;
+    float* part_re = a.partial + (int64_t)chunk * 2 * a.plane;
+    float* part_im = part_re + a.plane;
     bool first_flush = true;
     int64_t g = 0;
     for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -390,7 +323,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         ok = false;
         break;
       }
-      // B[(b,c), j] = e^{2 pi i (s_b y'_j + s_c z'_j + c_j)}, zero past the last point
+      // B[col, k] = e^{2 pi i (s_b y' + s_c z' + c)}, zero past the last column
       unsigned char* sB = ringB + bst * kSepBBytes;
       const float4* at = ring_atom[tst];
       auto form = [&](auto reduce_tag) {
@@ -433,8 +366,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         break;
       }
       tc_fence_after();
-      // TMEM lane = A row 2a + ri: this thread's row is Re T (ri = 0) or Im T
-      // (ri = 1) of point a, i.e. one plane of the partials
+      // TMEM lane = A row 2 pa + ri: this thread's row is Re D (ri = 0) or
+      // Im D (ri = 1) of row pa, i.e. one plane of the partials
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
@@ -443,10 +376,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         float* plane = (m_row & 1) ? part_im : part_re;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
-          const int64_t bc0 = nt * kSepN + col0 + cc;
-          float* dst = plane + pa * nbc + bc0;
-          const bool row_in = pa < a.n0 && bc0 < nbc;
-          const bool vec = row_in && bc0 + 32 <= nbc && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+          const int64_t bc0 = col_base + col0 + cc;
+          float* dst = plane + pa * a.ld + bc0;
+          const bool row_in = pa < a.n_rows && bc0 < col_end;
+          const bool vec = row_in && bc0 + 32 <= col_end && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
           // the partials' loads go out before the TMEM read
           float4 old[8];
 #pragma unroll
@@ -463,7 +396,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           } else if (row_in) {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (bc0 + q < nbc) dst[q] = (first_flush ? 0.f : dst[q]) + v[q];
+              if (bc0 + q < col_end) dst[q] = (first_flush ? 0.f : dst[q]) + v[q];
           }
         }
       }
@@ -480,9 +413,9 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       for (int tp = 0; tp < ntp; ++tp) {
         const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
         const int64_t pa = m_row >> 1;
-        if (pa < a.n0) {
-          float* dst = ((m_row & 1) ? part_im : part_re) + pa * nbc + nt * kSepN + col0;
-          for (int q = 0; q < 128 && nt * kSepN + col0 + q < nbc; ++q) dst[q] = 0.f;
+        if (pa < a.n_rows) {
+          float* dst = ((m_row & 1) ? part_im : part_re) + pa * a.ld + col_base + col0;
+          for (int q = 0; q < 128 && col_base + col0 + q < col_end; ++q) dst[q] = 0.f;
         }
       }
     }
@@ -541,6 +474,16 @@ __global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* _
 // -------------------------------------------------------------------------
 // host side
 // -------------------------------------------------------------------------
+
+cudaError_t sep_prepare_kernel() {
+  static_assert(kSepSmem + 4096 <= 227 * 1024, "dynamic + static shared memory of k_sep");
+  return cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem);
+}
+
+cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
+  k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
+  return cudaGetLastError();
+}
 
 namespace {
 
@@ -657,9 +600,7 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     if ((e = cudaMalloc(&p->d.sep_virt, virt_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc virtual map");
   }
   p->base_bytes += (int64_t)(a_bytes + part_bytes + chunk_bytes + virt_bytes);
-  static_assert(kSepSmem + 4096 <= 227 * 1024, "dynamic + static shared memory of k_sep");
-  if ((e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem)) != cudaSuccess)
-    return cuda_status(e, "separable shared memory attribute");
+  if ((e = sep_prepare_kernel()) != cudaSuccess) return cuda_status(e, "separable shared memory attribute");
   return SCATTER_OK;
 }
 
@@ -683,8 +624,10 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   }
   SepArgs a{};
   a.A = static_cast<const uint4*>(p->d.sep_A);
-  a.atom4 = p->d.atom4;
+  a.a_sp_stride = 0;
+  a.rec = p->d.atom4;
   a.chunks = p->d.sep_chunks;
+  a.ntiles = nullptr;
   a.bbox = p->d.inst_bbox;
   a.shift = p->d.inst_shift;
   a.smax_b = p->sep_smax[0];
@@ -693,17 +636,18 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.n0 = p->sep_n[0];
   a.n1 = p->sep_n[1];
   a.n2 = p->sep_n[2];
-  a.n_s = p->sep_ns;
-  a.n_slots = p->n_slots;
+  a.n_rows = p->sep_n[0];
+  a.ld = p->sep_n[1] * p->sep_n[2];
+  a.plane = p->sep_ns;
   a.n_steps = p->sep_steps;
   a.n_mt = p->sep_mt;
-  a.n_nt = p->sep_nt;
   a.partial = p->d.sep_partial;
   a.status = p->d.status;
   dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)n_chunks);
   timing_begin(p, st);
-  k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
+  const cudaError_t le = sep_launch_core(a, grid, st);
   timing_end(p, st);
+  if (le != cudaSuccess) return cuda_status(le, "separable kernel launch");
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
