@@ -114,12 +114,14 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a)
   }
 }
 
+// One warp: lane l sums the partials l, l + 32, ... in order, then a fixed
+// butterfly; the order does not depend on timing, so the loss is reproducible.
 __global__ void k_loss_final(const double* part, int n, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double v = 0.0;
-    for (int i = 0; i < n; ++i) v += part[i];
-    *out = v;
-  }
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int i = lane; i < n; i += 32) v += part[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) *out = v;
 }
 
 struct AdjArgs {

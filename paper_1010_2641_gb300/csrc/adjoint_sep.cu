@@ -21,7 +21,7 @@
 // k_adj_sep_scale  per (species, a): the exponents of the three rows' scales
 // k_adj_sep_tab    A blocks of every species in the tcgen05 no-swizzle layout
 // k_sep            U for every (M-tile pair, 256-atom tile, point chunk)
-// k_adj_sep_final  per atom: the sum over a and the chunks (FP64), gradient
+// k_adj_sep_final  per atom: the sum over a and the chunks, gradient
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -137,8 +137,22 @@ struct AdjSepFinalArgs {
   float* grad;             // [n_atoms][3] caller order
 };
 
+// Compensated FP32 accumulator (Neumaier): the running sum and its lost low part.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
 // One thread per atom slot of an N tile: the sum over a (and over the point
-// chunks) in FP64, then the rotation by e^{2 i pi c} and the H terms.
+// chunks) with FP32 products and compensated FP32 sums (FP64 runs at ~1/75
+// of the FP32 rate here; the 3 n0 terms are already contracted values whose
+// own error is ~1e-6), then the rotation by e^{2 i pi c} and the H terms in
+// FP64.  Four values of a per iteration keep 24 loads in flight per thread.
 __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f) {
   const Segment t = f.ntiles[blockIdx.x];
   const int64_t slot = t.begin + threadIdx.x;
@@ -148,42 +162,57 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
   const float4 at = f.atom4[slot];
   const int64_t rows = 3 * f.n0;
   const int* se = f.sexp + (int64_t)t.species * rows;
-  double V[2] = {0.0, 0.0}, Wd[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-  for (int64_t a = 0; a < f.n0; ++a) {
-    const float sa = f.axis_s[a];
-    const float ph = sa * at.x;
-    float sn, cs;
-    sincospif(2.0f * (ph - rintf(ph)), &sn, &cs);
-    double P[3][2];
+  CompSum V[2], Wd[3][2];
+  constexpr int kU = 4;
+  for (int64_t a0 = 0; a0 < f.n0; a0 += kU) {
+    float U[kU][3][2];
 #pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      const int64_t row = w * f.n0 + a;
-      double re = 0.0, im = 0.0;
-      for (int c = 0; c < f.n_chunks; ++c) {
-        re += (double)f.partial[((int64_t)(2 * c) * rows + row) * f.n_slots + slot];
-        im += (double)f.partial[((int64_t)(2 * c + 1) * rows + row) * f.n_slots + slot];
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        U[u][w][0] = U[u][w][1] = 0.f;
+        const int64_t a = a0 + u;
+        if (a < f.n0) {
+          const int64_t row = w * f.n0 + a;
+          for (int c = 0; c < f.n_chunks; ++c) {
+            U[u][w][0] += f.partial[((int64_t)(2 * c) * rows + row) * f.n_slots + slot];
+            U[u][w][1] += f.partial[((int64_t)(2 * c + 1) * rows + row) * f.n_slots + slot];
+          }
+        }
       }
-      const double sc = ldexp(1.0, se[row]);
-      re *= sc;
-      im *= sc;
-      P[w][0] = (double)cs * re - (double)sn * im;
-      P[w][1] = (double)cs * im + (double)sn * re;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t a = a0 + u;
+      if (a >= f.n0) break;
+      const float sa = f.axis_s[a];
+      const float ph = sa * at.x;
+      float sn, cs;
+      sincospif(2.0f * (ph - rintf(ph)), &sn, &cs);
+      float P[3][2];
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        const int k = se[w * f.n0 + a];
+        const float re = ldexpf(U[u][w][0], k), im = ldexpf(U[u][w][1], k);
+        P[w][0] = fmaf(cs, re, -sn * im);
+        P[w][1] = fmaf(cs, im, sn * re);
+      }
+      V[0].add(P[0][0]);
+      V[1].add(P[0][1]);
+      Wd[0][0].add(sa * P[0][0]);
+      Wd[0][1].add(sa * P[0][1]);
+      Wd[1][0].add(P[1][0]);
+      Wd[1][1].add(P[1][1]);
+      Wd[2][0].add(P[2][0]);
+      Wd[2][1].add(P[2][1]);
     }
-    V[0] += P[0][0];
-    V[1] += P[0][1];
-    Wd[0][0] += (double)sa * P[0][0];
-    Wd[0][1] += (double)sa * P[0][1];
-    Wd[1][0] += P[1][0];
-    Wd[1][1] += P[1][1];
-    Wd[2][0] += P[2][0];
-    Wd[2][1] += P[2][1];
   }
   double sn, cs;
   sincospi(2.0 * (double)at.w, &sn, &cs);
   const double scale = -2.0 * 3.14159265358979323846 * (double)f.atom_w[slot];
+  const double vr = V[0].value(), vi = V[1].value();
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double xr = f.H[d] * V[0] + Wd[d][0], xi = f.H[d] * V[1] + Wd[d][1];
+    const double xr = f.H[d] * vr + Wd[d][0].value(), xi = f.H[d] * vi + Wd[d][1].value();
     f.grad[3 * (int64_t)src + d] = (float)(scale * (cs * xi + sn * xr));  // Im(e^{2 i pi c} X)
   }
 }
