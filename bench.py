@@ -327,6 +327,10 @@ def run_gpu(args, rank, world, local_rank):
                 "kernel": "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)",
                 "kernel_ms": t_kern, "useful_tflops": useful / (t_kern * 1e-3) / 1e12,
                 "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+        # cross-check: this GPU's own f16 MMA rate (back-to-back tcgen05.mma, M=128 N=256, zero operands)
+        mb = api.microbench(8, iters=20000)
+        roof["f16_mma_microbench_tflops"] = mb["ops_per_s"] / 1e12
+        roof["frac_of_f16_mma_microbench"] = achieved / (mb["ops_per_s"] / 1e12)
     elif sm_mhz:
         peak = n_sm * MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR * sm_mhz * 1e6 / 1e9  # Gpair/s
         achieved = pairs / (t_kern * 1e-3) / 1e9

@@ -378,6 +378,9 @@ scatter_status scatter_amplitude_noalloc(int64_t n_atoms, const double* xyz, con
  *   2 fma.rn.f32 (lane-ops)              3 fma.rn.f32x2 (lane-ops)
  *   4 fma.rn.f64                         5 generic pair mix (2 MUFU + 7 FFMA)
  *   6 cvt.rni.f32.f32                    7 cvt.rn.f16x2.f32 (pack ops)
+ *   8 tcgen05.mma kind::f16 M=128 N=256 K=16 (dense f16 flop, one CTA per
+ *     SM; the separable path's contraction peak).  TIMEOUT if its bounded
+ *     completion wait gives up.
  * It allocates and frees a few KB of device memory and synchronises.
  */
 typedef struct scatter_microbench_result {

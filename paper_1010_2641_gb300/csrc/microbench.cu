@@ -15,6 +15,10 @@
 //   kind 5  2 MUFU + 7 FFMA per "pair"    (pairs: the generic-kernel mix)
 //   kind 6  cvt.rni.f32.f32               (round-to-integer ops)
 //   kind 7  cvt.rn.f16x2.f32              (pack ops: 2 floats -> f16x2)
+//   kind 8  tcgen05.mma kind::f16, M=128 N=256 K=16, operands in shared
+//           memory, FP32 accumulators in TMEM  (dense f16 flop): the peak
+//           of the separable path's contraction, one CTA per SM, one thread
+//           issuing back-to-back MMAs into two accumulators
 //
 // Every kernel runs a fixed number of independent dependency chains per thread
 // so that latency is hidden; results are written out so nothing is eliminated.
@@ -22,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include "device_common.cuh"
 #include "scatter_internal.h"
 
 namespace {
@@ -151,6 +156,66 @@ __global__ void ub_kernel(float* out, int iters, long long* cycles) {
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Dense f16 MMA rate: A (128 x 16) and B (256 x 16) zero-filled in the
+// canonical no-swizzle K-major layout, `iters` MMAs alternating between two
+// 128 x 256 FP32 accumulators, one commit at the end; the issuing thread
+// times the loop with clock64 (the MMA queue holds it back to the pipe's
+// rate).  A wait that gives up sets out[0] to -1.
+constexpr uint32_t kMbTcIdesc = (1u << 4) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint64_t mb_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__global__ void __launch_bounds__(128) ub_tc_kernel(float* out, int iters, long long* cycles) {
+  __shared__ __align__(1024) unsigned char sm[4096 + 8192];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (4096 + 8192) / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     scatter::dev::smem_addr(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    scatter::dev::mbar_init(&bar, 1);
+    scatter::dev::mbar_fence_init();
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    const uint64_t a = mb_desc(scatter::dev::smem_addr(sm), 2048, 128);
+    const uint64_t b = mb_desc(scatter::dev::smem_addr(sm + 4096), 4096, 128);
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+      const uint32_t d = tmem + (uint32_t)((it & 1) * 256);
+      const uint32_t acc = it >= 2 ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+          "l"(a), "l"(b), "r"(kMbTcIdesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     scatter::dev::smem_addr(&bar))
+                 : "memory");
+    const bool ok = scatter::dev::mbar_wait_bounded(&bar, 0);
+    cycles[blockIdx.x] = clock64() - t0;
+    if (!ok) out[0] = -1.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // Units of work per thread per iteration for each kind.
 double ops_per_iter(int kind) {
   switch (kind) {
@@ -162,6 +227,7 @@ double ops_per_iter(int kind) {
     case 5: return 1.0 * kChains;   // generic pairs
     case 6: return 2.0 * kChains;   // FRND
     case 7: return 2.0 * kChains;   // F2F pack
+    case 8: return 2.0 * 128 * 256 * 16;  // flop per MMA (per CTA, not per thread)
   }
   return 0.0;
 }
@@ -170,13 +236,14 @@ double ops_per_iter(int kind) {
 
 extern "C" scatter_status scatter_microbench(int kind, int iters,
                                              scatter_microbench_result* res) {
-  if (!res || kind < 0 || kind > 7 || iters <= 0) return SCATTER_ERR_INVALID_ARG;
+  if (!res || kind < 0 || kind > 8 || iters <= 0) return SCATTER_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCATTER_ERR_NO_DEVICE;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return SCATTER_ERR_CUDA;
-  const int threads = 256;
-  const int blocks_per_sm = 4;
+  // kind 8: one CTA per SM (each allocates all 512 TMEM columns)
+  const int threads = kind == 8 ? 128 : 256;
+  const int blocks_per_sm = kind == 8 ? 1 : 4;
   const int blocks = prop.multiProcessorCount * blocks_per_sm;
   float* out = nullptr;
   long long* cyc = nullptr;
@@ -184,6 +251,15 @@ extern "C" scatter_status scatter_microbench(int kind, int iters,
   if (cudaMalloc(&cyc, sizeof(long long) * blocks) != cudaSuccess) {
     cudaFree(out);
     return SCATTER_ERR_OOM;
+  }
+  cudaMemset(out, 0, sizeof(float));  // kind 8 flags a timed-out wait in out[0]
+  // kind 8: 120 KB of (unused) dynamic shared memory keeps one CTA per SM
+  constexpr int kTcSmem = 120 * 1024;
+  if (kind == 8 && cudaFuncSetAttribute(ub_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
+                       cudaSuccess) {
+    cudaFree(out);
+    cudaFree(cyc);
+    return SCATTER_ERR_CUDA;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -198,6 +274,7 @@ extern "C" scatter_status scatter_microbench(int kind, int iters,
       case 5: ub_kernel<5><<<blocks, threads>>>(out, n_iter, cyc); break;
       case 6: ub_kernel<6><<<blocks, threads>>>(out, n_iter, cyc); break;
       case 7: ub_kernel<7><<<blocks, threads>>>(out, n_iter, cyc); break;
+      case 8: ub_tc_kernel<<<blocks, threads, kTcSmem>>>(out, n_iter, cyc); break;
     }
   };
   launch(16);  // warm-up
@@ -209,6 +286,8 @@ extern "C" scatter_status scatter_microbench(int kind, int iters,
   cudaEventElapsedTime(&ms, e0, e1);
   long long* hcyc = new long long[blocks];
   cudaMemcpy(hcyc, cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
+  float flag = 0.f;
+  cudaMemcpy(&flag, out, sizeof(float), cudaMemcpyDeviceToHost);
   long long maxc = 0;
   for (int i = 0; i < blocks; ++i) maxc = hcyc[i] > maxc ? hcyc[i] : maxc;
   delete[] hcyc;
@@ -217,7 +296,8 @@ extern "C" scatter_status scatter_microbench(int kind, int iters,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return SCATTER_ERR_CUDA;
-  const double total = ops_per_iter(kind) * (double)iters * threads * blocks;
+  if (kind == 8 && flag < 0.f) return SCATTER_ERR_TIMEOUT;
+  const double total = ops_per_iter(kind) * (double)iters * (kind == 8 ? 1 : threads) * blocks;
   res->seconds = ms * 1e-3;
   res->ops_per_s = total / res->seconds;
   res->ops_per_clk_per_sm =
