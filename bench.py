@@ -567,9 +567,10 @@ def measure_paths(args, dev, clk, only=None):
         m_gid = 512 * 512 * 32
         res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
                               "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel",
-                              # 16 FFMA per (atom, point) for the four beams: 8 points = 32 beam-pairs per SM per clock
-                              "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 32.0, n_sm, clk, "Gbeam-pair/s",
-                                                     "alu", "beam-pairs (16 FFMA per atom-point, 128 FFMA/SM/clk)")}
+                              # 8 FFMA per (atom, point) for the four beams (they share the real products of
+                              # E and Z1, Z2): 16 points = 64 beam-pairs per SM per clock on the FMA pipe
+                              "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 64.0, n_sm, clk, "Gbeam-pair/s",
+                                                     "alu", "beam-pairs (8 FFMA per atom-point, 128 FFMA/SM/clk)")}
         del plan
         plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
                         gid=gid, path="separable", timing=True)

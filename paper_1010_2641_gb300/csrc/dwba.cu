@@ -15,9 +15,13 @@
 //                                                  (h,k), shared by 4 alpha_f
 //   Z1  = exp(2 i pi Sz1 z'), Z2 = exp(2 i pi Sz2 z'), Z3 = conj Z2, Z4 = conj Z1
 // Z1, Z2 depend on (atom, alpha_f) only: a per-call table (accurate sincospif)
-// streamed through shared memory by the TMA engine.  Per (atom, S point) the
-// four beams cost 16 FFMA; a warp's 32 lanes are 32 (h,k) points sharing the
-// same alpha_f values, so the table reads are shared-memory broadcasts.
+// streamed through shared memory by the TMA engine.  A warp's 32 lanes are
+// 32 (h,k) points sharing the same alpha_f values, so the table reads are
+// shared-memory broadcasts.  E Z and E conj(Z) are made of the same four real
+// products, E Z = (P - Q, R + T) and E conj(Z) = (P + Q, T - R) with
+// P = Er Zr, Q = Ei Zi, R = Er Zi, T = Ei Zr, and every beam is linear in the
+// atom sums, so the kernel accumulates P, Q, R, T of Z1 and Z2 (8 FFMA per
+// (atom, S point)) and forms the four beams once per 64-atom tile.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -146,11 +150,12 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
     const int cnt = (int)dev::min64(kDwbaTile, end - c_begin);
     const int st = k & 1;
     const bool ok = dev::mbar_wait_bounded(&sh_bar[st], (uint32_t)((k >> 1) & 1));
-    float2 acc[kDwbaR][4];
+    // tile sums of the four real products per Z: [P, Q, R, T] of Z1, then of Z2
+    float acc[kDwbaR][8];
 #pragma unroll
     for (int r = 0; r < kDwbaR; ++r)
 #pragma unroll
-      for (int t = 0; t < 4; ++t) acc[r][t] = make_float2(0.f, 0.f);
+      for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     if (ok) {
       const float4* zs = stage_z(st);
       const float4* as = stage_a(st);
@@ -166,26 +171,31 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
         const float4* zr = zs + j * kAfBlock + af_l0;
 #pragma unroll
         for (int r = 0; r < kDwbaR; ++r) {
-          const float4 z = zr[r];
-          // E Z1, E Z2, E conj(Z2), E conj(Z1)
-          acc[r][0].x = fmaf(er, z.x, fmaf(-ei, z.y, acc[r][0].x));
-          acc[r][0].y = fmaf(er, z.y, fmaf(ei, z.x, acc[r][0].y));
-          acc[r][1].x = fmaf(er, z.z, fmaf(-ei, z.w, acc[r][1].x));
-          acc[r][1].y = fmaf(er, z.w, fmaf(ei, z.z, acc[r][1].y));
-          acc[r][2].x = fmaf(er, z.z, fmaf(ei, z.w, acc[r][2].x));
-          acc[r][2].y = fmaf(ei, z.z, fmaf(-er, z.w, acc[r][2].y));
-          acc[r][3].x = fmaf(er, z.x, fmaf(ei, z.y, acc[r][3].x));
-          acc[r][3].y = fmaf(ei, z.x, fmaf(-er, z.y, acc[r][3].y));
+          const float4 z = zr[r];  // Z1 (re, im), Z2 (re, im)
+          acc[r][0] = fmaf(er, z.x, acc[r][0]);
+          acc[r][1] = fmaf(ei, z.y, acc[r][1]);
+          acc[r][2] = fmaf(er, z.y, acc[r][2]);
+          acc[r][3] = fmaf(ei, z.x, acc[r][3]);
+          acc[r][4] = fmaf(er, z.z, acc[r][4]);
+          acc[r][5] = fmaf(ei, z.w, acc[r][5]);
+          acc[r][6] = fmaf(er, z.w, acc[r][6]);
+          acc[r][7] = fmaf(ei, z.z, acc[r][7]);
         }
       }
     }
+    // beams of the tile: E Z1, E Z2, E conj(Z2), E conj(Z1)
 #pragma unroll
-    for (int r = 0; r < kDwbaR; ++r)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        seg[r][t].x += acc[r][t].x;
-        seg[r][t].y += acc[r][t].y;
-      }
+    for (int r = 0; r < kDwbaR; ++r) {
+      const float* q = acc[r];
+      seg[r][0].x += q[0] - q[1];
+      seg[r][0].y += q[2] + q[3];
+      seg[r][1].x += q[4] - q[5];
+      seg[r][1].y += q[6] + q[7];
+      seg[r][2].x += q[4] + q[5];
+      seg[r][2].y += q[7] - q[6];
+      seg[r][3].x += q[0] + q[1];
+      seg[r][3].y += q[3] - q[2];
+    }
     c_begin += cnt;
     if (c_begin >= end) {
       // fold W_t f_s(|S_t|) e^{2 pi i s_t . t} into the map
