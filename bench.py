@@ -462,7 +462,7 @@ def measure_paths(args, dev, clk, only=None):
     other = "generic" if args.path == "separable" else "separable"
 
     def want(name):
-        return only is None or only == name or (name == "dwba_island" and only.startswith("dwba_island"))
+        return only is None or only == name or (name == "dwba_island" and only == "dwba_island_separable")
 
     if want(f"{other}_sphere"):
         # generic FP32/MUFU kernel on the full strained-sphere map, with its roofline
@@ -556,6 +556,17 @@ def measure_paths(args, dev, clk, only=None):
             "workload": "strained cube 102400 atoms x 128^3, dL/dr on a SEPARABLE plan (k_sep, operands swapped)",
             "roofline": _tensor_roof_adjoint(128, 128 * 128, plan.info()["n_atoms_padded"], ms)}
         del plan, x, A, I_obs
+    if only == 'dwba_island_mid':
+        # profiling case of the FFMA DWBA kernel: 127,560-atom island (base 60, height 20 cells) x 128x128x32
+        isl = W.truncated_pyramid(base_cells=60, height_cells=20, top_cells=15)
+        gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
+        plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes(128, 128, 32)),
+                        atom_species=isl.species, gid=gid, path="generic", timing=True)
+        x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
+        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=2)
+        res["dwba_island_mid"] = {"value": 4 * len(isl.xyz) * 128 * 128 * 32 / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
+                                  "kernel_ms": ms, "workload": f"island {len(isl.xyz)} atoms x 128x128x32, FFMA kernel"}
+        del plan, x
     if want('dwba_island'):
         # grazing-incidence four-beam map of the island (1,013,496 atoms x 512x512x32)
         isl = W.truncated_pyramid()
