@@ -380,23 +380,31 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           float* dst = plane + pa * a.ld + bc0;
           const bool row_in = pa < a.n_rows && bc0 < col_end;
           const bool vec = row_in && bc0 + 32 <= col_end && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
-          // the partials' loads go out before the TMEM read
-          float4 old[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            old[q] = (vec && !first_flush) ? reinterpret_cast<const float4*>(dst)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
+          // the first read-out stores, later ones add in L2 (reductions, no
+          // load round trip); every element belongs to this CTA and its
+          // updates come from this thread in program order, so the sum is
+          // deterministic
           if (vec) {
             float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              d4[q] = make_float4(old[q].x + v[4 * q], old[q].y + v[4 * q + 1], old[q].z + v[4 * q + 2],
-                                  old[q].w + v[4 * q + 3]);
+            for (int q = 0; q < 8; ++q) {
+              const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              if (first_flush)
+                d4[q] = x;
+              else
+                atomicAdd(d4 + q, x);
+            }
           } else if (row_in) {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (bc0 + q < col_end) dst[q] = (first_flush ? 0.f : dst[q]) + v[q];
+              if (bc0 + q < col_end) {
+                if (first_flush)
+                  dst[q] = v[q];
+                else
+                  atomicAdd(dst + q, v[q]);
+              }
           }
         }
       }
