@@ -627,12 +627,17 @@ def measure_paths(args, dev, clk, only=None):
     if want('batch_ewald'):
         # batched persistent launch, CUDA-graph replay (64 uneven crystals)
         bx, bs, bcoef, bS, ao, so = W.ewald_batch()
-        plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True)
+        # tiles picked by the autotuner at plan time (the configuration's "autotuned tiles")
+        plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True,
+                        autotune=True)
         x = torch.tensor(bx, dtype=torch.float64, device=dev)
         out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
         ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
         pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
+        inf = plan.info()
         res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
+                              "tiling": {"threads": inf["threads"], "points_per_thread": inf["points_per_thread"],
+                                         "autotuned": True},
                               "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
                               "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
                                                      "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
