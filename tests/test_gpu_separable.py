@@ -113,3 +113,29 @@ def test_wide_grid_takes_the_reduced_phase_path():
     plan.check()
     ref = oracle.amplitude(c.xyz, W.grid_points(axes), c.coef, A_LAT, species=c.species)
     assert rel_l2(A, ref) < 1e-4
+
+
+def test_repeated_calls_are_bitwise_identical():
+    """Chunks of more than 256 steps read the accumulators out several times
+    (a store, then L2 reductions in program order): the map, and the
+    tensor-core gradient on the same plan, repeat bit for bit."""
+    c = W.fcc_sphere(radius_cells=8.0, seed=77)
+    axes = [W.linspace_axis(0.0, 40, step=0.004), W.linspace_axis(0.0, 9, step=0.004),
+            W.linspace_axis(4.0, 33, step=0.004)]
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="separable", split_k=1)
+    assert plan.info()["n_atoms_padded"] // 16 > 2 * 256  # several read-outs per chunk
+    x = torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0")
+    a1 = plan.amplitude(x).clone()
+    a2 = plan.amplitude(x)
+    plan.check()
+    assert torch.equal(a1, a2)
+    I_obs = (a1.abs() ** 2 * 1.02).float()
+    _, g1 = plan.backward(x, a1, I_obs)
+    g1 = g1.clone()
+    _, g2 = plan.backward(x, a1, I_obs)
+    plan.check()
+    assert torch.equal(g1, g2)
+    S = W.grid_points(axes)
+    idx = np.random.default_rng(5).choice(len(S), 256, replace=False)
+    ref = oracle.amplitude(c.xyz, S[idx], c.coef, A_LAT, species=c.species)
+    assert rel_l2(a1.cpu().numpy().astype(np.complex128)[idx], ref) < TOL_TC
