@@ -673,13 +673,27 @@ def run_sweep(args):
             e1.record()
             torch.cuda.synchronize()
             call_ms = e0.elapsed_time(e1)
+            # the same call on a plan without per-call timing replays its launch
+            # sequence as a CUDA graph (first call eager, second captures)
+            gplan = api.Plan(unit, W.LATTICE_A, n_atoms, s_list=S, path="generic", autotune=args.autotune)
+            for _ in range(3):
+                gplan.amplitude(x, out=out)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(5):
+                gplan.amplitude(x, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            graph_call_ms = e0.elapsed_time(e1) / 5
+            del gplan
             idx = sample_indices(n_s, min(n_s, 16), seed=3)
             ref = oracle.amplitude(xyz, S[idx], unit, W.LATTICE_A)
             got = out.cpu().numpy()[idx].astype(np.complex128)
             err = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
             info = plan.info()
             rows.append({"atoms": n_atoms, "reflections": n_s, "value": n_atoms * n_s / (ms * 1e-3),
-                         "kernel_ms": ms, "call_ms": call_ms, "rel_l2_16pts": err, "threads": info["threads"],
+                         "kernel_ms": ms, "call_ms": call_ms, "graph_call_ms": graph_call_ms,
+                         "rel_l2_16pts": err, "threads": info["threads"],
                          "points_per_thread": info["points_per_thread"], "split_k": info["split_k"],
                          "atoms_per_thread": info["atoms_per_thread"]})
             del plan, x, out

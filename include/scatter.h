@@ -152,9 +152,12 @@ typedef struct scatter_options {
   int32_t threads;           /* tile override: threads per CTA (0 = auto)     */
   int32_t points_per_thread; /* tile override: S points per thread (0 = auto) */
   int32_t split_k;           /* tile override: atom chunks per S tile (0 = auto) */
-  int32_t use_graph;         /* batches: capture the launch sequence in a CUDA
-                                graph on first use (default on: 0 = on,
-                                -1 = off)                                     */
+  int32_t use_graph;         /* capture a call's launch sequence (prep, main
+                                kernels, reduction) in a CUDA graph on first
+                                use and replay it while the pointer arguments
+                                stay the same (default on: 0 = on, -1 = off);
+                                single-instance plans with `timing` and the
+                                FP64 path run eagerly                         */
   int32_t timing;            /* 1: record CUDA events around the main kernel
                                 of every call (see scatter_plan_timing)       */
   int32_t atoms_per_thread;  /* generic path, one instance: 1, 2, 4, 8 or 16

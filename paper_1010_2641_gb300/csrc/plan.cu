@@ -185,6 +185,10 @@ void build_chunks(scatter_plan_s* p, int split_k) {
 scatter_status apply_tiling(scatter_plan_s* p, const Tiling& t) {
   if (!generic_tiling_supported(t)) return fail(SCATTER_ERR_INVALID_ARG, "unsupported tiling");
   p->tiling = t;
+  if (p->graph_exec) {  // a captured call graph holds the old launch shapes
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
   build_chunks(p, t.split_k);
   release(p->d.segs);
   release(p->d.chunk_seg_off);
