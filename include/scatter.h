@@ -283,6 +283,16 @@ scatter_status scatter_vjp(scatter_plan_t plan, const double* xyz, const float* 
                            const void* G, float* dL_dxyz, void* stream);
 
 /*
+ * scatter_selftest_wait — device self-check of the failure path: one thread
+ * waits for an mbarrier phase that nothing completes, gives up after ~2^20
+ * SM clocks (well under a millisecond) and sets the TIMEOUT bit of the plan's
+ * status word exactly as a pipeline wait of the kernels would; the next
+ * scatter_check returns SCATTER_ERR_TIMEOUT and clears the word, and the
+ * context stays usable.  Enqueued on `stream`; nothing else is touched.
+ */
+scatter_status scatter_selftest_wait(scatter_plan_t plan, void* stream);
+
+/*
  * scatter_check — wait for the plan's stream work and report any condition a
  * kernel recorded in the plan's device status word (a bounded wait that gave
  * up: TIMEOUT; a non-finite position or occupancy: NUMERIC).  Clears the

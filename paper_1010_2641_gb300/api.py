@@ -207,6 +207,11 @@ class Plan:
     def check(self, stream=None) -> None:
         B.check(B.lib().scatter_check(self._h, _stream(stream)), "scatter_check")
 
+    def selftest_wait(self, stream=None) -> None:
+        """Enqueue the device self-check of the bounded waits (the next check()
+        raises SCATTER_ERR_TIMEOUT)."""
+        B.check(B.lib().scatter_selftest_wait(self._h, _stream(stream)), "scatter_selftest_wait")
+
     def info(self) -> dict:
         inf = B.scatter_plan_info()
         B.check(B.lib().scatter_plan_get_info(self._h, ctypes.byref(inf)), "scatter_plan_get_info")

@@ -101,6 +101,7 @@ _PROTOTYPES = {
                                    c_void_p]),
     "scatter_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "scatter_check": (c_int32, [c_void_p, c_void_p]),
+    "scatter_selftest_wait": (c_int32, [c_void_p, c_void_p]),
     "scatter_error_bound": (c_int32, [c_void_p, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "scatter_plan_get_info": (c_int32, [c_void_p, ctypes.POINTER(scatter_plan_info)]),
     "scatter_plan_timing": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),

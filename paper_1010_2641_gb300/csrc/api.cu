@@ -2,6 +2,7 @@
 // backward / vjp, status check, error model and plan info.
 #include <cmath>
 #include <cstring>
+#include "device_common.cuh"
 #include "launch.h"
 #include "plan.h"
 
@@ -167,6 +168,32 @@ extern "C" scatter_status scatter_vjp(scatter_plan_t p, const double* xyz, const
   p->last_launches = 0;
   return launch_backward(p, xyz, occ, nullptr, nullptr, static_cast<const float2*>(G), nullptr, dL_dxyz,
                          static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+// Device self-check of the bounded waits: one thread waits for the first
+// phase of an mbarrier that nothing arrives at, gives up after `budget`
+// cycles and records TIMEOUT in the plan's status word, through the same
+// helpers as every pipeline wait of the library.
+__global__ void k_wait_selftest(unsigned* status, long long budget) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    dev::mbar_init(&bar, 1);
+    dev::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !dev::mbar_wait_bounded(&bar, 0u, budget)) dev::set_status(status, kStatusTimeout);
+}
+
+}  // namespace
+
+extern "C" scatter_status scatter_selftest_wait(scatter_plan_t p, void* stream) {
+  if (!p) return fail(SCATTER_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(p->d.status, 1LL << 20);
+  return cuda_status(cudaGetLastError(), "wait self-check launch");
 }
 
 extern "C" scatter_status scatter_check(scatter_plan_t p, void* stream) {
