@@ -29,6 +29,7 @@ template <class T>
 scatter_status upload(T** dst, const T* src, size_t n, int64_t* bytes) {
   *dst = nullptr;
   if (n == 0) return SCATTER_OK;
+  if (injected_alloc_failure()) return fail(SCATTER_ERR_OOM, "injected allocation failure (SCATTER_FAULT)");
   cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
   if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
   *bytes += (int64_t)(n * sizeof(T));

@@ -17,4 +17,10 @@ scatter_status cuda_status(cudaError_t e, const char* what);
 
 bool log_enabled();
 
+// Host-side fault injection for tests: with SCATTER_FAULT=alloc:N in the
+// environment the N-th device allocation of plan building (counted since the
+// variable last changed; plain "alloc" means the first) reports
+// out-of-memory before any device call.  No device work is involved.
+bool injected_alloc_failure();
+
 }  // namespace scatter

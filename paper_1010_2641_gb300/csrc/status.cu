@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include "scatter_internal.h"
 
 namespace scatter {
@@ -40,6 +42,25 @@ bool log_enabled() {
     flag = (v && v[0] == '1') ? 1 : 0;
   }
   return flag == 1;
+}
+
+bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string seen;
+  static long count = 0;
+  const char* v = getenv("SCATTER_FAULT");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!v || strncmp(v, "alloc", 5) != 0) {
+    seen.clear();
+    count = 0;
+    return false;
+  }
+  if (seen != v) {
+    seen = v;
+    count = 0;
+  }
+  const long n = v[5] == ':' ? atol(v + 6) : 1;
+  return ++count == n;
 }
 
 }  // namespace scatter

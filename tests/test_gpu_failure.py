@@ -54,3 +54,31 @@ def test_timeout_and_numeric_bits_are_distinct():
     with pytest.raises(B.ScatterError) as e:
         plan.check()
     assert e.value.status == B.SCATTER_ERR_TIMEOUT
+
+
+def _small_plan():
+    c = W.fcc_sphere(radius_cells=2.5, seed=99)
+    axes = [W.linspace_axis(0.0, 9, step=0.01), W.linspace_axis(0.0, 7, step=0.01), W.linspace_axis(4.0, 5, step=0.01)]
+    return c, axes, lambda: api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_injected_allocation_failure_is_reported_and_leaks_nothing(monkeypatch, n):
+    """SCATTER_FAULT=alloc:N fails the N-th device allocation of plan
+    building (host side): scatter_plan returns OOM, frees what it had
+    allocated, and a plan built afterwards works."""
+    c, axes, make = _small_plan()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    monkeypatch.setenv("SCATTER_FAULT", f"alloc:{n}")
+    with pytest.raises(B.ScatterError) as e:
+        make()
+    assert e.value.status == B.SCATTER_ERR_OOM
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 4 << 20
+    monkeypatch.delenv("SCATTER_FAULT")
+    plan = make()
+    A = plan.amplitude(torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0"))
+    plan.check()
+    ref = oracle.amplitude(c.xyz, W.grid_points(axes), c.coef, A_LAT, species=c.species)
+    assert rel_l2(A.cpu().numpy().astype(np.complex128).reshape(-1), ref) < 1e-4
