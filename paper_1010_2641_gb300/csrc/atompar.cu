@@ -37,8 +37,44 @@ struct ApArgs {
   float H[3];
   float inv4a2;
   const float2* ftab;     // Eq. 4 factor table [n_species][M], or null (form factors)
+  const unsigned long long* bbox;  // [6] this call's ordered min / max xyz
+  const double* shift;             // [3] the call's centring t
+  float smax[3];                   // max |S_d - H_d| over the points
   float2* partial;        // [block][M]
 };
+
+template <int K, bool EXACT>
+__device__ __forceinline__ void atompar_sums(const float4* sh_s, int np, const float (&x)[K], const float (&y)[K],
+                                             const float (&z)[K], const float (&c)[K], const float (&w)[K],
+                                             float2 (*sh_part)[kApPts], int lane, int warp) {
+  for (int p = 0; p < np; ++p) {
+    const float4 s = sh_s[p];
+    // two accumulator pairs halve the dependent FFMA chain
+    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(
+                                  s.x, x[k], dev::frac_product_plus(s.y, y[k], dev::frac_product_plus(s.z, z[k], c[k]))))
+                            : dev::frac_rn(fmaf(s.z, z[k], fmaf(s.y, y[k], fmaf(s.x, x[k], c[k]))));
+      float sn, cs;
+      dev::sincos_cycles_mufu(f, &sn, &cs);
+      if (k & 1) {
+        re1 = fmaf(w[k], cs, re1);
+        im1 = fmaf(w[k], sn, im1);
+      } else {
+        re0 = fmaf(w[k], cs, re0);
+        im0 = fmaf(w[k], sn, im0);
+      }
+    }
+    float re = re0 + re1, im = im0 + im1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) sh_part[warp][p] = make_float2(re, im);
+  }
+}
 
 template <int K>
 __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
@@ -76,31 +112,12 @@ __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
   }
   __syncthreads();
 
-  for (int p = 0; p < np; ++p) {
-    const float4 s = sh_s[p];
-    // two accumulator pairs halve the dependent FFMA chain
-    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float f = dev::frac_rn(fmaf(s.z, z[k], fmaf(s.y, y[k], fmaf(s.x, x[k], c[k]))));
-      float sn, cs;
-      dev::sincos_cycles_mufu(f, &sn, &cs);
-      if (k & 1) {
-        re1 = fmaf(w[k], cs, re1);
-        im1 = fmaf(w[k], sn, im1);
-      } else {
-        re0 = fmaf(w[k], cs, re0);
-        im0 = fmaf(w[k], sn, im0);
-      }
-    }
-    float re = re0 + re1, im = im0 + im1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
-    }
-    if (lane == 0) sh_part[warp][p] = make_float2(re, im);
-  }
+  // phases that can pass kPhaseExactLim cycles take the exact-product route
+  // (one decision per call: every CTA computes the same)
+  if (dev::phase_needs_exact(a.bbox, a.shift, a.smax))
+    atompar_sums<K, true>(sh_s, np, x, y, z, c, w, sh_part, lane, warp);
+  else
+    atompar_sums<K, false>(sh_s, np, x, y, z, c, w, sh_part, lane, warp);
   __syncthreads();
 
   // the block's T(S) for this tile, times f_s(|S|) of its species
@@ -216,6 +233,9 @@ scatter_status launch_atompar(scatter_plan_t p, float2* amp_out, float* int_out,
   for (int d = 0; d < 3; ++d) a.H[d] = (float)p->inst[0].H[d];
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.ftab = p->d.ftab;
+  a.bbox = p->d.inst_bbox;
+  a.shift = p->d.inst_shift;
+  for (int d = 0; d < 3; ++d) a.smax[d] = (float)p->s_max[d];
   a.partial = p->d.partial;
   dim3 grid((unsigned)((p->n_s + kApPts - 1) / kApPts), (unsigned)p->ap_n_blocks);
   void* args[] = {&a};

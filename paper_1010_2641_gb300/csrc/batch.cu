@@ -36,6 +36,8 @@ struct BatchArgs {
   int32_t n_items;
   const double* inst_H;
   const double* inst_shift;
+  const unsigned long long* inst_bbox;  // [batch][6] ordered min / max xyz of this call
+  float smax[3];                        // max |S_d - H_d| over every instance's points
   float inv4a2;
   int* counter;
   float2* partial;
@@ -78,10 +80,16 @@ __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
     }
     const int chunk = in.chunk0 + w.chunk;
     float2 tot[R];
-    if (!chunk_sum<kModeList, R>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk], a.chunk_seg_off[chunk + 1],
-                                 a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status, nullptr,
-                                 1, 0, 0))  // batches take no factor table
-      return;
+    // batches take no factor table; a long crystal takes the exact-product phases
+    const bool ok =
+        dev::phase_needs_exact(a.inst_bbox + 6 * w.inst, a.inst_shift + 3 * w.inst, a.smax)
+            ? chunk_sum<kModeList, R, true>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                            a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom,
+                                            sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0)
+            : chunk_sum<kModeList, R, false>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                             a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom,
+                                             sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+    if (!ok) return;
     const int64_t M_b = in.s_end - in.s_begin;
     const double* t = a.inst_shift + 3 * w.inst;
     const double* H64 = a.inst_H + 3 * w.inst;
@@ -287,6 +295,8 @@ scatter_status enqueue_batch_kernels(scatter_plan_t p, float2* amp, float* inten
   a.n_items = p->batch_items;
   a.inst_H = p->d.inst_H;
   a.inst_shift = p->d.inst_shift;
+  a.inst_bbox = p->d.inst_bbox;
+  for (int d = 0; d < 3; ++d) a.smax[d] = (float)p->s_max[d];
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.counter = p->d.counter;
   a.partial = p->d.partial;

@@ -36,6 +36,45 @@ __device__ __forceinline__ float frac_rn(float x) {
   return __fsub_rn(x, n);
 }
 
+// frac_rn(p) + (err + acc): a rounded value's fractional part, then its
+// rounding error and a small addend
+__device__ __forceinline__ float dev_frac_plus(float p, float err, float acc) {
+  return frac_rn(p) + (err + acc);
+}
+
+// Exact-product phases for long crystals.  A phase s . x' computed with FP32
+// products errs by up to |s . x'| 2^-24 cycles: below 128 cycles that is
+// under 8e-6 cycles (5e-5 rad) per pair, well inside the FP32 paths' 1e-4;
+// above it (crystals hundreds to thousands of cells long) the rounding of
+// the products, structured along a lattice row, sets the noise floor of the
+// map.  The kernels then restore each product's rounding error (exact by
+// FMA) after its integer part is removed.
+constexpr double kPhaseExactLim = 128.0;  // cycles
+
+// True when |s . x'| + |c| can exceed kPhaseExactLim for positions inside
+// `bbox` (ordered min xyz, max xyz) centred on `shift` with |s_d| <= smax_d;
+// false without atoms or without a box.
+__device__ __forceinline__ bool phase_needs_exact(const unsigned long long* bbox, const double* shift,
+                                                  const float* smax) {
+  if (!bbox) return false;
+  double b = 0.5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const unsigned long long lo = bbox[d], hi = bbox[3 + d];
+    if (lo == ~0ULL || hi == 0ULL) return false;
+    const double e = fmax(fabs(unordered(lo) - shift[d]), fabs(unordered(hi) - shift[d]));
+    b += (double)smax[d] * (e + 1.0);
+  }
+  return b > kPhaseExactLim;
+}
+
+// x - rint(x) of a product a b with its rounding error restored: the pair
+// (frac of the rounded product, exact error) summed into `acc`.
+__device__ __forceinline__ float frac_product_plus(float a, float b, float acc) {
+  const float p = a * b;
+  return dev_frac_plus(p, fmaf(a, b, -p), acc);
+}
+
 // sin and cos of 2*pi*f for |f| <= 1/2 (cycles) on the MUFU pipe
 // (sin.approx/cos.approx: absolute error below 1e-6 on [-pi, pi]).
 __device__ __forceinline__ void sincos_cycles_mufu(float f, float* s, float* c) {

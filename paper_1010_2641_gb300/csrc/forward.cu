@@ -194,10 +194,16 @@ __global__ void __launch_bounds__(THREADS) k_generic(const GenericArgs a) {
   const int64_t pstride = MODE == kModeGrid ? 1 : THREADS;
   float2 tot[R];
   int k = 0;
-  if (!chunk_sum<MODE, R>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk], a.chunk_seg_off[chunk + 1], a.coef,
-                          a.H, a.inv4a2, sx, sy, sz, sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase,
-                          pstride))
-    return;
+  // one decision per call (every CTA computes the same): phases that can
+  // pass kPhaseExactLim cycles take the exact-product route
+  const bool ok = dev::phase_needs_exact(a.bbox, a.shift, a.smax)
+                      ? chunk_sum<MODE, R, true>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                                 a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz,
+                                                 sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride)
+                      : chunk_sum<MODE, R, false>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                                  a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz,
+                                                  sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride);
+  if (!ok) return;
 
   // ---- epilogue -----------------------------------------------------------------
   if (a.partial) {
@@ -311,6 +317,8 @@ GenericArgs make_args(scatter_plan_t p) {
   }
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.shift = p->d.inst_shift;
+  a.bbox = p->d.inst_bbox;
+  for (int d = 0; d < 3; ++d) a.smax[d] = (float)p->s_max[d];
   a.ftab = p->d.ftab;
   a.status = p->d.status;
   return a;

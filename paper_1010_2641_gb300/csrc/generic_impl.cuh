@@ -26,6 +26,8 @@ struct GenericArgs {
   double H64[3];
   float inv4a2;
   const double* shift;    // [3] device, written by prep
+  const unsigned long long* bbox;  // [6] device, this call's ordered min / max xyz (null: never exact)
+  float smax[3];          // max |S_d - H_d| over the points
   const float2* ftab;     // Eq. 4 factor table [n_species][M], or null (form factors)
   float2* out_amp;
   float* out_int;
@@ -42,11 +44,13 @@ scatter_status launch_generic_args(GenericArgs a, int R, int threads, int n_chun
 // is the split phase + MUFU sincos + 2 FFMA into tile-blocked FP32 sums, and
 // f_s(|S|) is folded in at the end of every species segment (or, with an
 // Eq. 4 factor table, F_s(S) at the thread's point indices pbase + r pstride,
-// clamped to the map).  `k` counts the
+// clamped to the map).  EXACT: crystals whose phases can pass
+// dev::kPhaseExactLim cycles take every product of the phase with its
+// rounding error restored.  `k` counts the
 // tiles this CTA has consumed so far (it sets the stage and mbarrier parity
 // and carries over between chunks of a persistent CTA).  Returns false if a
 // wait gave up (the CTA then drains its copies and must stop).
-template <int MODE, int R>
+template <int MODE, int R, bool EXACT = false>
 __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, const float* __restrict__ atom_w,
                                           const Segment* __restrict__ segs, int seg_lo, int seg_hi,
                                           const float* __restrict__ coef, const float H[3], float inv4a2,
@@ -95,10 +99,12 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
         const float4 at = at4[j];
         const float w = atw[j];
         if (MODE == kModeGrid) {
-          const float base = fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
+          const float base = EXACT ? dev::frac_product_plus(sx[0], at.x, dev::frac_product_plus(sy[0], at.y, at.w))
+                                   : fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float f = dev::frac_rn(fmaf(sz[r], at.z, base));
+            const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(sz[r], at.z, base))
+                                  : dev::frac_rn(fmaf(sz[r], at.z, base));
             float sn, cs;
             dev::sincos_cycles_mufu(f, &sn, &cs);
             acc[r].x = fmaf(w, cs, acc[r].x);
@@ -107,7 +113,10 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float f = dev::frac_rn(fmaf(sz[r], at.z, fmaf(sy[r], at.y, fmaf(sx[r], at.x, at.w))));
+            const float f =
+                EXACT ? dev::frac_rn(dev::frac_product_plus(
+                            sx[r], at.x, dev::frac_product_plus(sy[r], at.y, dev::frac_product_plus(sz[r], at.z, at.w))))
+                      : dev::frac_rn(fmaf(sz[r], at.z, fmaf(sy[r], at.y, fmaf(sx[r], at.x, at.w))));
             float sn, cs;
             dev::sincos_cycles_mufu(f, &sn, &cs);
             acc[r].x = fmaf(w, cs, acc[r].x);
