@@ -132,6 +132,9 @@ struct AdjArgs {
   int64_t s_per_chunk;
   float* partial;          // [split][n_slots][3]
   int64_t n_slots;
+  const unsigned long long* bbox;  // [6] this call's ordered min / max xyz
+  const double* shift;             // [3] its centring t
+  float smax[3];                   // max |S_d - H_d| over the points
   unsigned* status;
 };
 
@@ -166,6 +169,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
   }
   __syncthreads();
   const int64_t n_tiles = m1 > m0 ? (m1 - m0 + kSTile - 1) / kSTile : 0;
+  // long crystals: every product of the phase with its rounding error restored
+  const bool exact = dev::phase_needs_exact(a.bbox, a.shift, a.smax);
   auto issue = [&](int64_t k) {
     if (k >= n_tiles) return;
     const int64_t b = m0 + k * kSTile;
@@ -194,7 +199,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
         const float4 q = sv[2 * j + 1];  // S, gF.im
 #pragma unroll
         for (int r = 0; r < kAdjRA; ++r) {
-          const float f = dev::frac_rn(fmaf(p.z, z[r], fmaf(p.y, y[r], fmaf(p.x, x[r], c[r]))));
+          const float f =
+              exact ? dev::frac_rn(dev::frac_product_plus(
+                          p.x, x[r], dev::frac_product_plus(p.y, y[r], dev::frac_product_plus(p.z, z[r], c[r]))))
+                    : dev::frac_rn(fmaf(p.z, z[r], fmaf(p.y, y[r], fmaf(p.x, x[r], c[r]))));
           float sn, cs;
           dev::sincos_cycles_mufu(f, &sn, &cs);
           const float v = fmaf(p.w, sn, q.w * cs);
@@ -285,7 +293,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     z[r] = at.z;
     c[r] = at.w;
     float sn, cs;
-    dev::sincos_cycles_mufu(dev::frac_rn(a.ds * z[r]), &sn, &cs);  // rotation per l step
+    dev::sincos_cycles_mufu(dev::frac_of_product(a.ds, z[r]), &sn, &cs);  // rotation per l step
     wr[r] = cs;
     wi[r] = sn;
   }
@@ -323,7 +331,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     float base[kAdjRA], er[kAdjRA], ei[kAdjRA], sv[kAdjRA], szv[kAdjRA];
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) {
-      base[r] = fmaf(sy, y[r], fmaf(sx, x[r], c[r]));
+      // once per atom and tile: the products with their rounding errors
+      base[r] = dev::frac_product_plus(sx, x[r], dev::frac_product_plus(sy, y[r], c[r]));
       sv[r] = szv[r] = 0.f;
     }
     if (ok) {
@@ -332,7 +341,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
         // exact exponential at the first point of every 64
         const float qz = sv4[jb].x;
 #pragma unroll
-        for (int r = 0; r < kAdjRA; ++r) dev::sincos_cycles_mufu(dev::frac_rn(fmaf(qz, z[r], base[r])), &ei[r], &er[r]);
+        for (int r = 0; r < kAdjRA; ++r)
+          dev::sincos_cycles_mufu(dev::frac_rn(dev::frac_product_plus(qz, z[r], base[r])), &ei[r], &er[r]);
         const int je = min(cnt, jb + kReseed);
 #pragma unroll 2
         for (int j = jb; j < je; ++j) {
@@ -536,6 +546,9 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
     aa.s_per_chunk = p->adj_s_per_chunk;
     aa.partial = p->d.adj_partial;
     aa.n_slots = p->n_slots;
+    aa.bbox = p->d.inst_bbox;
+    aa.shift = p->d.inst_shift;
+    for (int d = 0; d < 3; ++d) aa.smax[d] = (float)p->s_max[d];
     aa.status = p->d.status;
     if (p->adj_blocks > 0) {
       dim3 gridd((unsigned)p->adj_blocks, (unsigned)p->adj_split);

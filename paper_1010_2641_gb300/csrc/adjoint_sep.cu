@@ -185,9 +185,8 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
       const int64_t a = a0 + u;
       if (a >= f.n0) break;
       const float sa = f.axis_s[a];
-      const float ph = sa * at.x;
       float sn, cs;
-      sincospif(2.0f * (ph - rintf(ph)), &sn, &cs);
+      sincospif(2.0f * dev::frac_of_product(sa, at.x), &sn, &cs);
       float P[3][2];
 #pragma unroll
       for (int w = 0; w < 3; ++w) {

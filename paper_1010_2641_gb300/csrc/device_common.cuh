@@ -75,6 +75,13 @@ __device__ __forceinline__ float frac_product_plus(float a, float b, float acc) 
   return dev_frac_plus(p, fmaf(a, b, -p), acc);
 }
 
+// a b - rint(a b) with the product's rounding error restored (|result|
+// <= 1/2 + 2^-24 |a b|): the argument of the per-call tables' sincospif
+__device__ __forceinline__ float frac_of_product(float a, float b) {
+  const float p = a * b;
+  return (p - rintf(p)) + fmaf(a, b, -p);
+}
+
 // sin and cos of 2*pi*f for |f| <= 1/2 (cycles) on the MUFU pipe
 // (sin.approx/cos.approx: absolute error below 1e-6 on [-pi, pi]).
 __device__ __forceinline__ void sincos_cycles_mufu(float f, float* s, float* c) {

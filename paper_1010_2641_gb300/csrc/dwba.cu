@@ -58,6 +58,8 @@ struct DwbaArgs {
   double H64[3];
   float inv4a2;
   const double* shift;
+  const unsigned long long* bbox;  // [6] this call's ordered min / max xyz
+  float smax[3];                   // max |s_h|, |s_k| over the map (z: the table's business), 0
   float2* out_amp;
   float* out_int;
   float2* partial;
@@ -81,10 +83,40 @@ __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float* __r
   }
   const float z = atom4[slot].z;
   float s1, c1, s2, c2;
-  const float p1 = sz[af] * z, p2 = sz[n_af + af] * z;
-  sincospif(2.0f * (p1 - rintf(p1)), &s1, &c1);
-  sincospif(2.0f * (p2 - rintf(p2)), &s2, &c2);
+  sincospif(2.0f * dev::frac_of_product(sz[af], z), &s1, &c1);
+  sincospif(2.0f * dev::frac_of_product(sz[n_af + af], z), &s2, &c2);
   ztab[i] = make_float4(c1, s1, c2, s2);
+}
+
+// Tile sums of the four real products of E_j = w_j e^{2 pi i (s_h x'_j + s_k y'_j + c_j)}
+// with each Z of the thread's rows: [P, Q, R, T] of Z1, then of Z2.  EXACT: the
+// phase with its products' rounding errors restored (long crystals).
+template <bool EXACT>
+__device__ __forceinline__ void dwba_tile_products(const float4* zs, const float4* as, const float* ws, int cnt,
+                                                   int af_l0, float sh, float sk, float (&acc)[kDwbaR][8]) {
+#pragma unroll 2
+  for (int j = 0; j < cnt; ++j) {
+    const float4 at = as[j];
+    const float w = ws[j];
+    const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(sh, at.x, dev::frac_product_plus(sk, at.y, at.w)))
+                          : dev::frac_rn(fmaf(sk, at.y, fmaf(sh, at.x, at.w)));
+    float sn, cs;
+    dev::sincos_cycles_mufu(f, &sn, &cs);
+    const float er = w * cs, ei = w * sn;
+    const float4* zr = zs + j * kAfBlock + af_l0;
+#pragma unroll
+    for (int r = 0; r < kDwbaR; ++r) {
+      const float4 z = zr[r];  // Z1 (re, im), Z2 (re, im)
+      acc[r][0] = fmaf(er, z.x, acc[r][0]);
+      acc[r][1] = fmaf(ei, z.y, acc[r][1]);
+      acc[r][2] = fmaf(er, z.y, acc[r][2]);
+      acc[r][3] = fmaf(ei, z.x, acc[r][3]);
+      acc[r][4] = fmaf(er, z.z, acc[r][4]);
+      acc[r][5] = fmaf(ei, z.w, acc[r][5]);
+      acc[r][6] = fmaf(er, z.w, acc[r][6]);
+      acc[r][7] = fmaf(ei, z.z, acc[r][7]);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
@@ -145,6 +177,8 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
   int64_t c_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin : 0;
   int k = 0;
   bool aborted = false;
+  // long crystals: the per-atom phase with its products' rounding errors restored
+  const bool exact = dev::phase_needs_exact(a.bbox, a.shift, a.smax);
   while (c_seg < seg_hi) {
     const int64_t end = a.segs[c_seg].end;
     const int cnt = (int)dev::min64(kDwbaTile, end - c_begin);
@@ -157,31 +191,11 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     if (ok) {
-      const float4* zs = stage_z(st);
-      const float4* as = stage_a(st);
-      const float* ws = stage_w(st);
-#pragma unroll 2
-      for (int j = 0; j < cnt; ++j) {
-        const float4 at = as[j];
-        const float w = ws[j];
-        const float f = dev::frac_rn(fmaf(sk, at.y, fmaf(sh, at.x, at.w)));
-        float sn, cs;
-        dev::sincos_cycles_mufu(f, &sn, &cs);
-        const float er = w * cs, ei = w * sn;
-        const float4* zr = zs + j * kAfBlock + af_l0;
-#pragma unroll
-        for (int r = 0; r < kDwbaR; ++r) {
-          const float4 z = zr[r];  // Z1 (re, im), Z2 (re, im)
-          acc[r][0] = fmaf(er, z.x, acc[r][0]);
-          acc[r][1] = fmaf(ei, z.y, acc[r][1]);
-          acc[r][2] = fmaf(er, z.y, acc[r][2]);
-          acc[r][3] = fmaf(ei, z.x, acc[r][3]);
-          acc[r][4] = fmaf(er, z.z, acc[r][4]);
-          acc[r][5] = fmaf(ei, z.w, acc[r][5]);
-          acc[r][6] = fmaf(er, z.w, acc[r][6]);
-          acc[r][7] = fmaf(ei, z.z, acc[r][7]);
-        }
-      }
+      // one branch per tile: the loop bodies are compiled apart
+      if (exact)
+        dwba_tile_products<true>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
+      else
+        dwba_tile_products<false>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
     }
     // beams of the tile: E Z1, E Z2, E conj(Z2), E conj(Z1)
 #pragma unroll
@@ -465,6 +479,10 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   }
   a.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   a.shift = p->d.inst_shift;
+  a.bbox = p->d.inst_bbox;
+  a.smax[0] = (float)p->s_max[0];
+  a.smax[1] = (float)p->s_max[1];
+  a.smax[2] = 0.f;  // the Z table takes exact products itself
   a.n_s = p->n_s;
   a.status = p->d.status;
   const int n_chunks = (int)p->chunk_seg_off.size() - 1;

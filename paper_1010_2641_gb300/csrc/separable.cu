@@ -82,8 +82,7 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
     const int64_t slot = ks * kSepStep + kb * 4 + q;
     float sn = 0.f, cs = 0.f;
     if (a < t.n0) {
-      const float p = sa * t.atom4[slot].x;
-      sincospif(2.0f * (p - rintf(p)), &sn, &cs);
+      sincospif(2.0f * dev::frac_of_product(sa, t.atom4[slot].x), &sn, &cs);
       const float w = t.atom_w[slot];
       sn *= w;
       cs *= w;
@@ -297,13 +296,17 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     // kSepPhaseLim cycles when the centred extent is small: the exact mod-1
     // reduction is then skipped (MUFU sin/cos of an argument of L cycles errs
     // by ~L 2^-24 cycles, 6e-6 rad at the limit, below this path's 1e-4)
-    bool reduce = true;
+    // (and above dev::kPhaseExactLim cycles, crystals hundreds of cells long,
+    // each product is taken with its rounding error restored)
+    bool reduce = true, exact = false;
     {
       const unsigned long long ylo = a.bbox[1], zlo = a.bbox[2], yhi = a.bbox[4], zhi = a.bbox[5];
       if (ylo != ~0ULL && zlo != ~0ULL && yhi != 0ULL && zhi != 0ULL) {
         const double ey = fmax(fabs(dev::unordered(ylo) - a.shift[1]), fabs(dev::unordered(yhi) - a.shift[1]));
         const double ez = fmax(fabs(dev::unordered(zlo) - a.shift[2]), fabs(dev::unordered(zhi) - a.shift[2]));
-        reduce = (double)a.smax_b * (ey + 1.0) + (double)a.smax_c * (ez + 1.0) + 0.5 > kSepPhaseLim;
+        const double bound = (double)a.smax_b * (ey + 1.0) + (double)a.smax_c * (ez + 1.0) + 0.5;
+        reduce = bound > kSepPhaseLim;
+        exact = bound > dev::kPhaseExactLim;
       }
     }
     float* part_re = a.partial + (int64_t)chunk * 2 * a.plane;
@@ -326,8 +329,9 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       // B[col, k] = e^{2 pi i (s_b y' + s_c z' + c)}, zero past the last column
       unsigned char* sB = ringB + bst * kSepBBytes;
       const float4* at = ring_atom[tst];
-      auto form = [&](auto reduce_tag) {
-        constexpr bool kReduce = decltype(reduce_tag)::value;
+      // mode 0: raw phase, 1: reduced mod 1, 2: exact products, reduced
+      auto form = [&](auto mode_tag) {
+        constexpr int kMode = decltype(mode_tag)::value;
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
           uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
@@ -335,8 +339,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const float4 v = at[kb * 4 + q];
-              const float p = fmaf(sb, v.y, fmaf(sc, v.z, v.w));
-              const float ph = kReduce ? dev::frac_rn(p) : p;
+              const float ph =
+                  kMode == 2 ? dev::frac_rn(dev::frac_product_plus(sb, v.y, dev::frac_product_plus(sc, v.z, v.w)))
+                  : kMode == 1 ? dev::frac_rn(fmaf(sb, v.y, fmaf(sc, v.z, v.w)))
+                               : fmaf(sb, v.y, fmaf(sc, v.z, v.w));
               float sn, cs;
               dev::sincos_cycles_mufu(ph, &sn, &cs);
               split2(cs, sn, hi[q], lo[q]);
@@ -346,10 +352,12 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       };
-      if (reduce)
-        form(std::true_type{});
+      if (exact)
+        form(std::integral_constant<int, 2>{});
+      else if (reduce)
+        form(std::integral_constant<int, 1>{});
       else
-        form(std::false_type{});
+        form(std::integral_constant<int, 0>{});
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
