@@ -119,7 +119,13 @@ __device__ __forceinline__ void dwba_tile_products(const float4* zs, const float
   }
 }
 
+// Launched twice per call, EXACT = false and true: every CTA of a call
+// reaches the same phase bound, and the instance that does not match it
+// returns at once, so each loop body is compiled on its own.
+template <bool EXACT>
 __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
+  // long crystals: the per-atom phase with its products' rounding errors restored
+  if (dev::phase_needs_exact(a.bbox, a.shift, a.smax) != EXACT) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t sh_bar[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -177,8 +183,6 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
   int64_t c_begin = seg_lo < seg_hi ? a.segs[seg_lo].begin : 0;
   int k = 0;
   bool aborted = false;
-  // long crystals: the per-atom phase with its products' rounding errors restored
-  const bool exact = dev::phase_needs_exact(a.bbox, a.shift, a.smax);
   while (c_seg < seg_hi) {
     const int64_t end = a.segs[c_seg].end;
     const int cnt = (int)dev::min64(kDwbaTile, end - c_begin);
@@ -191,11 +195,7 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     if (ok) {
-      // one branch per tile: the loop bodies are compiled apart
-      if (exact)
-        dwba_tile_products<true>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
-      else
-        dwba_tile_products<false>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
+      dwba_tile_products<EXACT>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
     }
     // beams of the tile: E Z1, E Z2, E conj(Z2), E conj(Z1)
 #pragma unroll
@@ -372,9 +372,10 @@ std::complex<double> fresnel_r(double alpha, double delta, double beta) {
 int dwba_blocks_per_sm() {
   static int cached = 0;
   if (cached) return cached;
-  cudaFuncSetAttribute(k_dwba, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwbaSmem);
+  cudaFuncSetAttribute(k_dwba<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwbaSmem);
+  cudaFuncSetAttribute(k_dwba<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwbaSmem);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dwba, kDwbaThreads, kDwbaSmem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dwba<false>, kDwbaThreads, kDwbaSmem) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
   }
@@ -495,9 +496,10 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   dwba_blocks_per_sm();  // sets the dynamic shared memory attribute
   dim3 grid((unsigned)((p->n_axis[0] * p->n_axis[1] + 31) / 32), (unsigned)n_afb, (unsigned)std::max(n_chunks, 1));
   timing_begin(p, st);
-  k_dwba<<<grid, kDwbaThreads, kDwbaSmem, st>>>(a);
+  k_dwba<false><<<grid, kDwbaThreads, kDwbaSmem, st>>>(a);
+  k_dwba<true><<<grid, kDwbaThreads, kDwbaSmem, st>>>(a);
   timing_end(p, st);
-  p->last_launches += 1;
+  p->last_launches += 2;
   if (n_chunks > 1) {
     k_dwba_reduce<<<(unsigned)((p->n_s + 255) / 256), 256, 0, st>>>(p->d.partial, n_chunks, p->n_s, amp_out, int_out);
     p->last_launches += 1;
