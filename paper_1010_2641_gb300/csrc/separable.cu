@@ -232,6 +232,14 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     }
   } else if (mma_warp) {
     if (lane == 0) {
+      // descriptors of A stage 0 tile 0 and B stage 0 (hi and lo of the two
+      // K16 halves); other stages and tiles add their byte offset / 16 to the
+      // address field (every shared-memory address here is below 2^18)
+      const uint32_t a0 = dev::smem_addr(ringA), b0 = dev::smem_addr(ringB);
+      const uint64_t dah[2] = {smem_desc(a0, 2048, 128), smem_desc(a0 + 4096, 2048, 128)};
+      const uint64_t dal[2] = {smem_desc(a0 + 8192, 2048, 128), smem_desc(a0 + 8192 + 4096, 2048, 128)};
+      const uint64_t dbh[2] = {smem_desc(b0, 4096, 128), smem_desc(b0 + 8192, 4096, 128)};
+      const uint64_t dbl[2] = {smem_desc(b0 + 16384, 4096, 128), smem_desc(b0 + 16384 + 8192, 4096, 128)};
       int64_t flushes = 0;  // groups read out before the current one
       int64_t g = 0;
       for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -251,20 +259,16 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t aB = dev::smem_addr(ringB + bst * kSepBBytes);
+        const uint64_t offB = (uint64_t)((bst * kSepBBytes) >> 4);
         for (int tp = 0; tp < ntp; ++tp) {
-          const uint32_t aA = dev::smem_addr(ringA + (ast * kSepPair + tp) * kSepABytes);
+          const uint64_t offA = (uint64_t)(((ast * kSepPair + tp) * kSepABytes) >> 4);
           const uint32_t d = tmem + (uint32_t)(tp * kSepN);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const uint64_t a_hi = smem_desc(aA + u * 4096, 2048, 128);
-            const uint64_t a_lo = smem_desc(aA + 8192 + u * 4096, 2048, 128);
-            const uint64_t b_hi = smem_desc(aB + u * 8192, 4096, 128);
-            const uint64_t b_lo = smem_desc(aB + 16384 + u * 8192, 4096, 128);
             const uint32_t acc0 = (ks > grp.grp_start || u > 0) ? 1u : 0u;
-            mma_f16(d, a_hi, b_hi, acc0);
-            mma_f16(d, a_hi, b_lo, 1u);
-            mma_f16(d, a_lo, b_hi, 1u);
+            mma_f16(d, dah[u] + offA, dbh[u] + offB, acc0);
+            mma_f16(d, dah[u] + offA, dbl[u] + offB, 1u);
+            mma_f16(d, dal[u] + offA, dbh[u] + offB, 1u);
           }
         }
         mma_commit(&bar_done[ast]);
