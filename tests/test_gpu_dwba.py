@@ -116,3 +116,24 @@ def test_ge_dot_map_sampled(path, tol):
     ref = oracle.dwba(c.xyz, gid_points(axes)[idx], c.coef, A_LAT, LAM, W.GID_ALPHA_I, W.GID_DELTA, W.GID_BETA,
                       species=c.species)
     assert rel_l2(A[idx], ref) < tol
+
+
+@pytest.mark.parametrize("path,tol", [("generic", 1e-3), ("separable", 1e-3)])
+def test_long_chain_takes_exact_phases(path, tol):
+    """A 20,000-atom in-plane chain (displaced by N(0, 0.02) cells) with h
+    within +-0.1 of the reference reflection: |s_h x'| reaches ~1000 cycles,
+    far above the 128 cycles from which the FP32 kernels take each phase
+    product with its rounding error restored, so the FFMA kernel's exact
+    instance and the separable path's exact formation mode run here."""
+    n = 20000
+    xyz = W.linear_chain(n, sigma=0.02, seed=21)
+    xyz[:, 0] -= n / 2  # centred: the extent after centring is what the phase bound uses
+    c = W.Crystal(xyz=xyz, species=np.zeros(n, np.int32), coef=W.unit_species()[None])
+    axes = [4.0 + 0.0005 + 0.005 * np.arange(-20, 21), np.array([-0.01, 0.0, 0.01]), np.deg2rad(np.array([0.1, 0.25, 0.4, 0.7]))]
+    assert 0.1 * (n / 2) > 128  # the phase bound of this case, in cycles
+    A, _ = gpu_map(c, axes, path=path)
+    ref = oracle.dwba(c.xyz, gid_points(axes), c.coef, A_LAT, LAM, W.GID_ALPHA_I, W.GID_DELTA, W.GID_BETA,
+                      species=c.species)
+    err = rel_l2(A, ref)
+    print(f"long DWBA chain ({path}): rel L2 {err:.1e}")
+    assert err < tol
