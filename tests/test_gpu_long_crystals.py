@@ -1,0 +1,114 @@
+"""Long crystals on the S-list kernels: a displaced 20,000-atom chain along x
+with reflections within +-0.1 r.l.u. of (400) makes phases of ~1000 cycles,
+above the 128 cycles from which every FP32 kernel takes each phase product
+with its rounding error restored.  These cases run the exact branches of
+the generic list kernel, the atom-parallel kernel and the batched
+persistent kernel (an uneven batch whose first instance is the chain),
+against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle
+from closed_forms import rel_l2
+from paper_1010_2641_gb300 import api
+from paper_1010_2641_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+A_LAT = W.LATTICE_A
+N_CHAIN = 20000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def chain():
+    xyz = W.linear_chain(N_CHAIN, sigma=0.02, seed=31)
+    return xyz, np.zeros(N_CHAIN, np.int32), W.unit_species()[None]
+
+
+def reflections(m, seed):
+    rng = np.random.default_rng(seed)
+    S = np.zeros((m, 3))
+    S[:, 0] = 4.0 + rng.uniform(-0.1, 0.1, m)
+    S[:, 1:] = rng.uniform(-0.02, 0.02, (m, 2))
+    return S
+
+
+def run(plan, xyz):
+    A = plan.amplitude(torch.tensor(xyz, dtype=torch.float64, device="cuda:0"))
+    plan.check()
+    return A.cpu().numpy().astype(np.complex128)
+
+
+def test_phase_bound_of_the_cases():
+    # |s_x| <= 0.1 over a chain of half-length N/2 after centring: far above 128 cycles
+    assert 0.1 * (N_CHAIN / 2) > 128
+
+
+@pytest.mark.parametrize("atoms_per_thread", [0, 4])  # 0: the S-parallel list kernel, 4: atom-parallel
+def test_chain_on_list_kernels(atoms_per_thread):
+    xyz, sp, coef = chain()
+    S = reflections(4000 if atoms_per_thread == 0 else 40, seed=32)  # 4000: the heuristic keeps S-parallel
+    plan = api.Plan(coef, A_LAT, N_CHAIN, s_list=S, atom_species=sp, path="generic",
+                    atoms_per_thread=atoms_per_thread)
+    assert plan.info()["atoms_per_thread"] == atoms_per_thread
+    err = rel_l2(run(plan, xyz), oracle.amplitude(xyz, S, coef, A_LAT, species=sp))
+    print(f"long chain, list, atoms_per_thread={atoms_per_thread}: rel L2 {err:.1e}")
+    assert err < 1e-3
+
+
+def test_chain_in_a_batch():
+    xyz0, sp0, coef = chain()
+    c = W.fcc_sphere(radius_cells=3.0, seed=33)
+    xyz = np.concatenate([xyz0, c.xyz])
+    sp = np.zeros(len(xyz), np.int32)
+    S0, S1 = reflections(500, seed=34), W.ewald_slice(700, seed=35)
+    S = np.concatenate([S0, S1])
+    ao = np.array([0, N_CHAIN, len(xyz)], np.int64)
+    so = np.array([0, len(S0), len(S)], np.int64)
+    plan = api.Plan(coef, A_LAT, len(xyz), s_list=S, atom_species=sp, atom_off=ao, s_off=so)
+    A = run(plan, xyz)
+    err0 = rel_l2(A[:len(S0)], oracle.amplitude(xyz0, S0, coef, A_LAT, species=sp0))
+    err1 = rel_l2(A[len(S0):], oracle.amplitude(c.xyz, S1, coef, A_LAT, species=sp[N_CHAIN:]))
+    print(f"batch: long chain rel L2 {err0:.1e}, sphere {err1:.1e}")
+    assert err0 < 1e-3
+    assert err1 < 1e-4
+
+
+@pytest.mark.parametrize("form", ["list", "atom_parallel", "batch"])
+def test_paper_chain_dynamic_range_on_list_kernels(form):
+    """The paper's accuracy test (Section 2.3) on the S-list kernels: a perfect
+    1e5-atom chain at x = 0..N-1, H every 0.001 r.l.u. from 0.98 to 1.02.  The
+    closed form is N at H = 1 and zero at every other point, so the peak over
+    the largest value at the zeros is the kernel's dynamic range: ~2e14 with
+    exact phase products, ~7e6 with single FP32 products."""
+    n = 100000
+    xyz = W.linear_chain(n)
+    coef = W.unit_species()[None]
+    H = 1.0 + 0.001 * np.arange(-20, 21)
+    S = np.zeros((len(H), 3))
+    S[:, 0] = H
+    if form == "list":
+        S = np.tile(S, (100, 1))  # 4100 points: the heuristic keeps the S-parallel kernel
+    if form == "batch":
+        c = W.fcc_sphere(radius_cells=2.5, seed=36)
+        S1 = W.ewald_slice(300, seed=37)
+        plan = api.Plan(coef, A_LAT, n + len(c.xyz), s_list=np.concatenate([S, S1]),
+                        atom_species=np.zeros(n + len(c.xyz), np.int32),
+                        atom_off=np.array([0, n, n + len(c.xyz)], np.int64),
+                        s_off=np.array([0, len(S), len(S) + len(S1)], np.int64))
+        A = run(plan, np.concatenate([xyz, c.xyz]))[:len(S)]
+    else:
+        plan = api.Plan(coef, A_LAT, n, s_list=S, path="generic", atoms_per_thread=4 if form == "atom_parallel" else 0)
+        assert (plan.info()["atoms_per_thread"] > 0) == (form == "atom_parallel")
+        A = run(plan, xyz)
+    I = (np.abs(A) ** 2)[:41]
+    assert abs(I[20] / n ** 2 - 1.0) < 1e-5
+    dr = I[20] / np.delete(I, 20).max()
+    print(f"paper chain N=1e5 on the {form} kernel: dynamic range {dr:.2e}")
+    assert dr > 1e10
