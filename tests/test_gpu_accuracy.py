@@ -95,11 +95,12 @@ def test_separable_chain_dynamic_range(axis):
     assert dr > 1e8
 
 
-@pytest.mark.parametrize("kind", ["line", "list"])
+@pytest.mark.parametrize("kind", ["line", "list", "separable"])
 def test_long_chain_gradient(kind):
-    """The FP32 adjoints on a 2e4-atom displaced chain (phases of thousands of
-    cycles): the line kernel's per-tile bases and re-seeds take exact
-    products, the list kernel its exact-product route; against the oracle."""
+    """The adjoints on a 2e4-atom displaced chain (phases of thousands of
+    cycles): the FP32 line kernel's per-tile bases and re-seeds take exact
+    products, the list kernel its exact-product route, and on a SEPARABLE
+    plan the tensor-core adjoint's final rotation; against the oracle."""
     import oracle
     from closed_forms import rel_l2
     N = 20000
@@ -109,15 +110,16 @@ def test_long_chain_gradient(kind):
     S = np.stack([np.zeros_like(l), np.zeros_like(l), l], 1)
     coef = W.unit_species()[None]
     I_obs = (np.abs(oracle.amplitude(pert, S, coef, A_LAT)) ** 2).astype(np.float32)
-    if kind == "line":
-        plan = api.Plan(coef, A_LAT, N, axes=[np.array([0.0]), np.array([0.0]), l], path="generic")
+    if kind in ("line", "separable"):
+        plan = api.Plan(coef, A_LAT, N, axes=[np.array([0.0]), np.array([0.0]), l],
+                        path="generic" if kind == "line" else "separable")
     else:
         plan = api.Plan(coef, A_LAT, N, s_list=S, path="generic")
     x = torch.tensor(xyz, dtype=torch.float64, device="cuda:0")
     A = plan.amplitude(x)
     loss, grad = plan.backward(x, A, torch.tensor(I_obs, device="cuda:0"))
     plan.check()
-    assert plan.info()["adjoint_form"] == (2 if kind == "line" else 1)
+    assert plan.info()["adjoint_form"] == {"line": 2, "list": 1, "separable": 3}[kind]
     L_ref, g_ref = oracle.loss_grad(xyz, S, I_obs, coef, A_LAT)
     err = rel_l2(grad.cpu().numpy(), g_ref)
     print(f"long chain gradient ({kind}): loss rel {abs(loss.item() - L_ref) / L_ref:.1e}, gradient rel L2 {err:.1e}")
