@@ -35,6 +35,7 @@ import os
 import pathlib
 import re
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -93,14 +94,15 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, log_dir: str | None = None):
         self.proc = None
         self.gpu = gpu_index
-        self.path = ROOT / "gpurun_out" / f"clocks_rank{gpu_index}.csv"
+        base = pathlib.Path(log_dir) if log_dir else pathlib.Path(tempfile.gettempdir())
+        self.path = base / f"clocks_rank{gpu_index}.csv"
 
     def start(self):
         try:
-            self.path.parent.mkdir(exist_ok=True)
+            self.path.parent.mkdir(parents=True, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -241,7 +243,7 @@ def run_gpu(args, rank, world, local_rank):
     c, axes = workload()
     n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
     pairs = n_atoms * n_s
-    cache = str(ROOT / "gpurun_out" / "tune_cache.jsonl") if args.autotune else None
+    cache = str(pathlib.Path(args.log_dir or tempfile.gettempdir()) / "tune_cache.jsonl") if args.autotune else None
     plan = api.Plan(c.coef, 5.43, n_atoms, axes=axes, atom_species=c.species, timing=True, path=args.path,
                     autotune=args.autotune and args.path == "generic", tune_cache=cache)
     info = plan.info()
@@ -261,7 +263,7 @@ def run_gpu(args, rank, world, local_rank):
     plan.check()
 
     # ---- device-timed region: K steps, L2 flushed between steps -------------
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(local_rank, args.log_dir)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kern_ms, launches = [], 0
@@ -712,6 +714,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--log-dir", default=None,
+                    help="folder for the per-rank clock samples and the autotune cache (default: the temp folder)")
     ap.add_argument("--no-paths", action="store_true", help="skip the other rows' measurements")
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
     ap.add_argument("--sweep", default=None, help="speed sweep over atoms x reflections, e.g. 100,1000,10000")
