@@ -628,19 +628,20 @@ def measure_paths(args, dev, clk, only=None):
         del x
     if want('batch_ewald'):
         # batched persistent launch, CUDA-graph replay (64 uneven crystals)
-        bx, bs, bcoef, bS, ao, so = W.ewald_batch()
+        bx, bs, bcoef, bS, ao, so = W.ewald_batch(n_instances=args.batch_instances)
         # tiles picked by the autotuner at plan time (the configuration's "autotuned tiles")
+        bcache = str(pathlib.Path(args.log_dir) / "tune_cache_batch.jsonl") if args.log_dir else None
         plan = api.Plan(bcoef, W.LATTICE_A, len(bx), s_list=bS, atom_species=bs, atom_off=ao, s_off=so, timing=True,
-                        autotune=True)
+                        autotune=True, tune_cache=bcache)
         x = torch.tensor(bx, dtype=torch.float64, device=dev)
         out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
         ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
         pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
         inf = plan.info()
-        res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms,
+        res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms, "instances": len(ao) - 1,
                               "tiling": {"threads": inf["threads"], "points_per_thread": inf["points_per_thread"],
                                          "autotuned": True},
-                              "workload": "64 fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
+                              "workload": f"{len(ao) - 1} fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
                               "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
                                                      "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
     return res
@@ -714,6 +715,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=64,
+                    help="crystals in the batch row (fewer: a smaller profiling case of the same kernel)")
     ap.add_argument("--log-dir", default=None,
                     help="folder for the per-rank clock samples and the autotune cache (default: the temp folder)")
     ap.add_argument("--no-paths", action="store_true", help="skip the other rows' measurements")
