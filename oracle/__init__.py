@@ -16,6 +16,8 @@ Every function below follows the paper's definitions:
                reading, the paper prints none)
   loss_grad    L = sum (|A|^2 - I_obs)^2 and its analytic gradient
   fd_grad      central finite differences of L (a second route to the gradient)
+  loss_grad_atoms  L and the analytic gradient of selected atoms from a map
+               the caller already has (large maps summed once)
 """
 from __future__ import annotations
 
@@ -63,6 +65,8 @@ def _load():
         lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
         lib.oracle_fd_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, i64, P, f64, P]
+        lib.oracle_loss_grad_given_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, i64, P, P, P]
+        lib.oracle_fd_grad_given_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, i64, P, f64, P]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
@@ -180,14 +184,42 @@ def loss_grad(xyz, S, I_obs, coef, lattice_a, species=None, occ=None, grad=True)
     return loss.value, g
 
 
-def fd_grad(xyz, S, I_obs, coef, lattice_a, atoms, h=1e-5, species=None, occ=None) -> np.ndarray:
-    """Central-difference gradient of L for the selected atoms, [len(atoms),3]."""
+def _amp2(A, n_s):
+    A = np.asarray(A, dtype=np.complex128).reshape(n_s)
+    return np.ascontiguousarray(np.stack([A.real, A.imag], -1))
+
+
+def fd_grad(xyz, S, I_obs, coef, lattice_a, atoms, h=1e-5, species=None, occ=None, A=None) -> np.ndarray:
+    """Central-difference gradient of L for the selected atoms, [len(atoms),3].
+    A: the unperturbed map from ``amplitude`` (computed here when None)."""
     xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
     S = _f64(S, 3)
     I_obs = _f64(I_obs).reshape(S.shape[0])
     sel = np.ascontiguousarray(np.asarray(atoms, dtype=np.int64))
     out = np.zeros((sel.shape[0], 3))
-    _load().oracle_fd_grad(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
-                           float(lattice_a), S.shape[0], _ptr(S), _ptr(I_obs), sel.shape[0], _ptr(sel),
-                           float(h), _ptr(out))
+    if A is None:
+        _load().oracle_fd_grad(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                               float(lattice_a), S.shape[0], _ptr(S), _ptr(I_obs), sel.shape[0], _ptr(sel),
+                               float(h), _ptr(out))
+    else:
+        A2 = _amp2(A, S.shape[0])
+        _load().oracle_fd_grad_given_amplitude(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0],
+                                               _ptr(coef), float(lattice_a), S.shape[0], _ptr(S), _ptr(A2),
+                                               _ptr(I_obs), sel.shape[0], _ptr(sel), float(h), _ptr(out))
     return out
+
+
+def loss_grad_atoms(xyz, S, A, I_obs, coef, lattice_a, atoms, species=None, occ=None):
+    """(L, dL/dr [len(atoms),3]) from a map A the caller already has (the
+    output of ``amplitude``): the formula of ``loss_grad`` for selected atoms."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    S = _f64(S, 3)
+    I_obs = _f64(I_obs).reshape(S.shape[0])
+    A2 = _amp2(A, S.shape[0])
+    sel = np.ascontiguousarray(np.asarray(atoms, dtype=np.int64))
+    loss = ctypes.c_double()
+    g = np.zeros((sel.shape[0], 3))
+    _load().oracle_loss_grad_given_amplitude(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                                             float(lattice_a), S.shape[0], _ptr(S), _ptr(A2), _ptr(I_obs),
+                                             sel.shape[0], _ptr(sel), ctypes.byref(loss), _ptr(g))
+    return loss.value, g

@@ -244,6 +244,43 @@ void oracle_dwba(int64_t n_atoms, const double* xyz, const int32_t* species,
   }
 }
 
+/* g(S) = 4 (|A|^2 - I_obs) conj(A) at every reflection, and the misfit
+ * L = sum_S (|A(S)|^2 - I_obs(S))^2 (serial sum in reflection order). */
+static double misfit_and_g(int64_t n_s, const double* A, const double* I_obs, double* g) {
+  double L = 0.0;
+  for (int64_t m = 0; m < n_s; ++m) {
+    const double I = A[2 * m] * A[2 * m] + A[2 * m + 1] * A[2 * m + 1];
+    const double d = I - I_obs[m];
+    L += d * d;
+    g[2 * m] = 4.0 * d * A[2 * m];
+    g[2 * m + 1] = -4.0 * d * A[2 * m + 1];
+  }
+  return L;
+}
+
+/* dL/dr_j of one atom:
+ *   -2 pi sum_S S * Im( g(S) w_j f_{s(j)}(|S|) exp(2 i pi S.r_j) ). */
+static void grad_one_atom(const double* r, double w, const double* coef_s, double lattice_a,
+                          int64_t n_s, const double* S, const double* g, double* out) {
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int64_t m = 0; m < n_s; ++m) {
+    const double* Sm = S + 3 * m;
+    double fr, fi;
+    oracle_form_factor(coef_s, s_norm(Sm, lattice_a), &fr, &fi);
+    const double phase = 2.0 * kPi * (Sm[0] * r[0] + Sm[1] * r[1] + Sm[2] * r[2]);
+    const double c = cos(phase), s = sin(phase);
+    /* e = w f (c + i s);  Im(g e) */
+    const double er = w * (fr * c - fi * s), ei = w * (fr * s + fi * c);
+    const double im_ge = g[2 * m] * ei + g[2 * m + 1] * er;
+    gx += Sm[0] * im_ge;
+    gy += Sm[1] * im_ge;
+    gz += Sm[2] * im_ge;
+  }
+  out[0] = -2.0 * kPi * gx;
+  out[1] = -2.0 * kPi * gy;
+  out[2] = -2.0 * kPi * gz;
+}
+
 /*
  * Misfit of an intensity map and its analytic gradient (adjoint of Eq. 2):
  *   L = sum_S (|A(S)|^2 - I_obs(S))^2
@@ -259,41 +296,40 @@ void oracle_loss_grad(int64_t n_atoms, const double* xyz, const int32_t* species
   double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
   double* g = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
   oracle_amplitude(n_atoms, xyz, species, occ, n_species, coef, lattice_a, n_s, S, A);
-  double L = 0.0;
-  for (int64_t m = 0; m < n_s; ++m) {
-    const double I = A[2 * m] * A[2 * m] + A[2 * m + 1] * A[2 * m + 1];
-    const double d = I - I_obs[m];
-    L += d * d;
-    g[2 * m] = 4.0 * d * A[2 * m];
-    g[2 * m + 1] = -4.0 * d * A[2 * m + 1];
-  }
-  *loss = L;
+  *loss = misfit_and_g(n_s, A, I_obs, g);
   if (grad) {
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t j = 0; j < n_atoms; ++j) {
-        const double* r = xyz + 3 * j;
-        const double w = occ ? occ[j] : 1.0;
-        const int32_t sp = species ? species[j] : 0;
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int64_t m = 0; m < n_s; ++m) {
-          const double* Sm = S + 3 * m;
-          double fr, fi;
-          oracle_form_factor(coef + ORACLE_NCOEF * sp, s_norm(Sm, lattice_a), &fr, &fi);
-          const double phase = 2.0 * kPi * (Sm[0] * r[0] + Sm[1] * r[1] + Sm[2] * r[2]);
-          const double c = cos(phase), s = sin(phase);
-          /* e = w f (c + i s);  Im(g e) */
-          const double er = w * (fr * c - fi * s), ei = w * (fr * s + fi * c);
-          const double im_ge = g[2 * m] * ei + g[2 * m + 1] * er;
-          gx += Sm[0] * im_ge;
-          gy += Sm[1] * im_ge;
-          gz += Sm[2] * im_ge;
-        }
-        grad[3 * j] = -2.0 * kPi * gx;
-        grad[3 * j + 1] = -2.0 * kPi * gy;
-        grad[3 * j + 2] = -2.0 * kPi * gz;
-    }
+    for (int64_t j = 0; j < n_atoms; ++j)
+      grad_one_atom(xyz + 3 * j, occ ? occ[j] : 1.0, coef + ORACLE_NCOEF * (species ? species[j] : 0),
+                    lattice_a, n_s, S, g, grad + 3 * j);
   }
   free(A);
+  free(g);
+}
+
+/*
+ * The same misfit and analytic gradient, for the selected atoms only and from
+ * an amplitude map A [n_s][2] the caller already has (oracle_amplitude's
+ * output): for maps too large to sum more than once.
+ *  atoms [n_sel] indices; grad out [n_sel][3] (may be NULL), *loss out.
+ */
+void oracle_loss_grad_given_amplitude(int64_t n_atoms, const double* xyz, const int32_t* species,
+                                      const double* occ, int32_t n_species, const double* coef,
+                                      double lattice_a, int64_t n_s, const double* S, const double* A,
+                                      const double* I_obs, int64_t n_sel, const int64_t* atoms,
+                                      double* loss, double* grad) {
+  (void)n_atoms;
+  (void)n_species;
+  double* g = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
+  *loss = misfit_and_g(n_s, A, I_obs, g);
+  if (grad) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < n_sel; ++q) {
+      const int64_t j = atoms[q];
+      grad_one_atom(xyz + 3 * j, occ ? occ[j] : 1.0, coef + ORACLE_NCOEF * (species ? species[j] : 0),
+                    lattice_a, n_s, S, g, grad + 3 * q);
+    }
+  }
   free(g);
 }
 
@@ -306,15 +342,17 @@ void oracle_loss_grad(int64_t n_atoms, const double* xyz, const int32_t* species
  *   L+ - L- = sum_S (I+ - I-) (I+ + I- - 2 I_obs)
  * (difference of squares: no cancellation between two large sums).
  *   grad_d = (L+ - L-) / (2 h).
+ * A [n_s][2] is the unperturbed map (oracle_amplitude's output).
  *
  *  atoms [n_sel] indices; grad out [n_sel][3].
  */
-void oracle_fd_grad(int64_t n_atoms, const double* xyz, const int32_t* species,
-                    const double* occ, int32_t n_species, const double* coef,
-                    double lattice_a, int64_t n_s, const double* S, const double* I_obs,
-                    int64_t n_sel, const int64_t* atoms, double h, double* grad) {
-  double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
-  oracle_amplitude(n_atoms, xyz, species, occ, n_species, coef, lattice_a, n_s, S, A);
+void oracle_fd_grad_given_amplitude(int64_t n_atoms, const double* xyz, const int32_t* species,
+                                    const double* occ, int32_t n_species, const double* coef,
+                                    double lattice_a, int64_t n_s, const double* S, const double* A,
+                                    const double* I_obs, int64_t n_sel, const int64_t* atoms, double h,
+                                    double* grad) {
+  (void)n_atoms;
+  (void)n_species;
   for (int64_t q = 0; q < n_sel; ++q) {
     const int64_t j = atoms[q];
     const double* r = xyz + 3 * j;
@@ -352,6 +390,17 @@ void oracle_fd_grad(int64_t n_atoms, const double* xyz, const int32_t* species,
       grad[3 * q + d] = diff / (2.0 * h);
     }
   }
+}
+
+/* oracle_fd_grad_given_amplitude with A computed here by oracle_amplitude. */
+void oracle_fd_grad(int64_t n_atoms, const double* xyz, const int32_t* species,
+                    const double* occ, int32_t n_species, const double* coef,
+                    double lattice_a, int64_t n_s, const double* S, const double* I_obs,
+                    int64_t n_sel, const int64_t* atoms, double h, double* grad) {
+  double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
+  oracle_amplitude(n_atoms, xyz, species, occ, n_species, coef, lattice_a, n_s, S, A);
+  oracle_fd_grad_given_amplitude(n_atoms, xyz, species, occ, n_species, coef, lattice_a, n_s, S, A, I_obs,
+                                 n_sel, atoms, h, grad);
   free(A);
 }
 

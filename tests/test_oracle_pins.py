@@ -321,6 +321,41 @@ def test_gradient_vs_finite_differences():
         assert np.max(np.abs(fd - g[sel])) < 1e-6 * np.max(np.abs(g[sel]))
 
 
+def test_gradient_from_a_given_map_two_atoms_closed_form():
+    """The selected-atom gradient from a map the caller already has (used for
+    maps too large to sum twice) against the two-atom closed form."""
+    rng = np.random.default_rng(34)
+    xyz = np.array([[0.3, -0.2, 1.1], [1.4, 0.9, -0.6]])
+    S = rng.uniform(-2, 2, (64, 3))
+    I_obs = rng.uniform(0, 4, 64)
+    A = oracle.amplitude(xyz, S, unit_coef(), A_LAT)
+    L, g = oracle.loss_grad_atoms(xyz, S, A, I_obs, unit_coef(), A_LAT, atoms=[1, 0])
+    ph = 2 * math.pi * (S @ (xyz[0] - xyz[1]))
+    I = 2 + 2 * np.cos(ph)
+    assert abs(L - np.sum((I - I_obs) ** 2)) < 1e-10 * L
+    g1 = (2 * (I - I_obs) * (-2 * np.sin(ph)) * 2 * math.pi) @ S
+    assert np.allclose(g[1], g1, rtol=1e-11, atol=1e-9)
+    assert np.allclose(g[0], -g1, rtol=1e-11, atol=1e-9)
+
+
+def test_gradient_from_a_given_map_vs_finite_differences():
+    """Both given-map routes (analytic and central differences) agree, with
+    species and occupancy, at two step sizes."""
+    rng = np.random.default_rng(35)
+    c = W.fcc_sphere(radius_cells=2.6, seed=8)
+    S = rng.uniform(-0.2, 0.2, (400, 3)) + np.array([0, 0, 4.0])
+    pert = W.perturbed_copy(c, 0.03, seed=9)
+    I_obs = np.abs(oracle.amplitude(pert.xyz, S, c.coef, A_LAT, pert.species)) ** 2
+    occ = rng.uniform(0.5, 1.0, len(c.xyz))
+    A = oracle.amplitude(c.xyz, S, c.coef, A_LAT, c.species, occ)
+    sel = rng.choice(len(c.xyz), 10, replace=False)
+    L, g = oracle.loss_grad_atoms(c.xyz, S, A, I_obs, c.coef, A_LAT, sel, species=c.species, occ=occ)
+    assert abs(L - np.sum((np.abs(A) ** 2 - I_obs) ** 2)) < 1e-12 * L
+    for h in (1e-5, 5e-6):
+        fd = oracle.fd_grad(c.xyz, S, I_obs, c.coef, A_LAT, sel, h=h, species=c.species, occ=occ, A=A)
+        assert np.max(np.abs(fd - g)) < 1e-6 * np.max(np.abs(g))
+
+
 def test_gradient_translation_invariance():
     """L depends on |A|^2 only, which a global translation leaves unchanged,
     so the gradients of all atoms sum to zero."""
