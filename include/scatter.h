@@ -355,8 +355,10 @@ const char* scatter_last_error(void);
  *
  * Computes T(S) = sum_j w_j exp(+2 i pi S . r_j) for a list of S points with
  * the generic FP32/MUFU kernel (f == 1: the per-species sum that a caller
- * multiplies by f_s(|S|) itself).  Positions are used as given (no integer
- * centring), so keep the crystal near the origin for best precision.
+ * multiplies by f_s(|S|) itself).  Positions are centred and split as on the
+ * plan path (integer centre of their bounding box), and crystals whose
+ * phases can pass 128 cycles take the exact-product phases, so the result
+ * holds the FP32 paths' accuracy wherever the crystal sits.
  *
  *  n_atoms     0 .. 524,288            n_s  0 .. 1,048,576
  *  xyz         device float64 [n_atoms][3] (lattice units)
@@ -367,13 +369,20 @@ const char* scatter_last_error(void);
  *  T_out       device complex64 [n_s], written in full
  *  stream      cudaStream_t or NULL
  *
- * Scratch: one file-scope __device__ array of 32 MiB per GPU (held from
- * the library's loading until process exit), shared by every call; calls
- * that overlap on the GPU race on it and must be serialised by the caller.
- * The first call on a device looks the array up (cudaGetSymbolAddress)
- * with that device current: make it before any stream capture.  Sizes
- * beyond the limits return SCATTER_ERR_INVALID_ARG without launching;
- * non-finite positions or occupancies contribute nothing.
+ * Errors: there is no plan to carry a status word, so failures found on the
+ * GPU poison the output instead: if any position, occupancy or S point is
+ * not finite, or a bounded wait inside the kernel gave up, every element of
+ * T_out is NaN.  Sizes beyond the limits return SCATTER_ERR_INVALID_ARG
+ * without launching.
+ *
+ * Scratch: one file-scope __device__ array of 48 MiB per GPU (held from the
+ * moment the library's device code is loaded on that GPU until process
+ * exit), shared by every call; calls that overlap on the GPU race on it and
+ * must be serialised by the caller.  Each call resets what it reads first.
+ * The first call on a device looks the array up (cudaGetSymbolAddress) with
+ * that device current; with lazy module loading that first call may also
+ * load the library's device code there and reserve the 48 MiB, so make it
+ * before any stream capture or allocation-free section begins.
  */
 scatter_status scatter_amplitude_noalloc(int64_t n_atoms, const double* xyz, const float* occ, int64_t n_s,
                                          const double* S, const double* center_hkl, void* T_out, void* stream);

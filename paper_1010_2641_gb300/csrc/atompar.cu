@@ -26,12 +26,15 @@ constexpr int kApPts = 128;  // reflections per CTA tile
 
 struct ApArgs {
   const float4* atom4;
+  const float4* atom_lo;  // position rounding errors (exact-product phases)
   const float* atom_w;
   const Segment* blocks;  // species-uniform atom blocks of <= kApThreads * K slots
   const float* coef;
   int64_t n_s;
   const float* s_hi;      // LIST [3][M]
+  const float* s_lo;      // LIST [3][M] rounding error of s_hi
   const float* axis_s;    // GRID [n0 | n1 | n2]
+  const float* axis_lo;   // GRID [n0 | n1 | n2] rounding error of axis_s
   int64_t n0, n1, n2;
   int grid_mode;
   float H[3];
@@ -43,18 +46,30 @@ struct ApArgs {
   float2* partial;        // [block][M]
 };
 
+// EXACT: the phase with its products' rounding errors restored and s and the
+// positions as double-floats; the positions' low parts are read from L1
+// (atom_lo at the thread's slots) rather than held in registers, which keeps
+// the plain loop's register allocation.
 template <int K, bool EXACT>
-__device__ __forceinline__ void atompar_sums(const float4* sh_s, int np, const float (&x)[K], const float (&y)[K],
-                                             const float (&z)[K], const float (&c)[K], const float (&w)[K],
+__device__ __forceinline__ void atompar_sums(const float4* sh_s, const float4* sh_slo, int np, const float (&x)[K],
+                                             const float (&y)[K], const float (&z)[K], const float (&c)[K],
+                                             const float (&w)[K], const float4* __restrict__ lo_base, int nk,
                                              float2 (*sh_part)[kApPts], int lane, int warp) {
   for (int p = 0; p < np; ++p) {
     const float4 s = sh_s[p];
+    const float4 sl = EXACT ? sh_slo[p] : s;
     // two accumulator pairs halve the dependent FFMA chain
     float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(
-                                  s.x, x[k], dev::frac_product_plus(s.y, y[k], dev::frac_product_plus(s.z, z[k], c[k]))))
+      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (EXACT && k < nk) e = __ldg(lo_base + k * kApThreads);  // slots past the block's end: weight 0
+      const float f = EXACT ? dev::frac_rn(dev::frac_product2_plus(
+                                  s.x, sl.x, x[k],
+                                  dev::frac_product2_plus(
+                                      s.y, sl.y, y[k],
+                                      dev::frac_product2_plus(s.z, sl.z, z[k],
+                                                              fmaf(s.x, e.x, fmaf(s.y, e.y, fmaf(s.z, e.z, c[k])))))))
                             : dev::frac_rn(fmaf(s.z, z[k], fmaf(s.y, y[k], fmaf(s.x, x[k], c[k]))));
       float sn, cs;
       dev::sincos_cycles_mufu(f, &sn, &cs);
@@ -79,6 +94,7 @@ __device__ __forceinline__ void atompar_sums(const float4* sh_s, int np, const f
 template <int K>
 __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
   __shared__ float4 sh_s[kApPts];
+  __shared__ float4 sh_slo[kApPts];  // rounding errors of sh_s (exact-product phases)
   __shared__ float2 sh_part[kApWarps][kApPts];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Segment blk = a.blocks[blockIdx.y];
@@ -88,14 +104,17 @@ __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
   // the tile's S offsets s = S - H
   for (int i = tid; i < np; i += kApThreads) {
     const int64_t m = p0 + i;
-    float4 s;
+    float4 s, sl;
     if (a.grid_mode) {
       const int64_t i2 = m % a.n2, line = m / a.n2, i1 = line % a.n1, i0 = line / a.n1;
       s = make_float4(a.axis_s[i0], a.axis_s[a.n0 + i1], a.axis_s[a.n0 + a.n1 + i2], 0.f);
+      sl = make_float4(a.axis_lo[i0], a.axis_lo[a.n0 + i1], a.axis_lo[a.n0 + a.n1 + i2], 0.f);
     } else {
       s = make_float4(a.s_hi[m], a.s_hi[a.n_s + m], a.s_hi[2 * a.n_s + m], 0.f);
+      sl = make_float4(a.s_lo[m], a.s_lo[a.n_s + m], a.s_lo[2 * a.n_s + m], 0.f);
     }
     sh_s[i] = s;
+    sh_slo[i] = sl;
   }
   // this thread's atoms (zero weight past the block's end)
   float x[K], y[K], z[K], c[K], w[K];
@@ -115,9 +134,11 @@ __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
   // phases that can pass kPhaseExactLim cycles take the exact-product route
   // (one decision per call: every CTA computes the same)
   if (dev::phase_needs_exact(a.bbox, a.shift, a.smax))
-    atompar_sums<K, true>(sh_s, np, x, y, z, c, w, sh_part, lane, warp);
+    atompar_sums<K, true>(sh_s, sh_slo, np, x, y, z, c, w, a.atom_lo + blk.begin + tid,
+                          (int)dev::max64(0, (blk.end - blk.begin - tid + kApThreads - 1) / kApThreads), sh_part, lane,
+                          warp);
   else
-    atompar_sums<K, false>(sh_s, np, x, y, z, c, w, sh_part, lane, warp);
+    atompar_sums<K, false>(sh_s, sh_slo, np, x, y, z, c, w, a.atom_lo, 0, sh_part, lane, warp);
   __syncthreads();
 
   // the block's T(S) for this tile, times f_s(|S|) of its species
@@ -220,11 +241,14 @@ scatter_status launch_atompar(scatter_plan_t p, float2* amp_out, float* int_out,
   if (!fn || !p->d.ap_blocks) return fail(SCATTER_ERR_UNSUPPORTED, "atom-parallel tiling not prepared");
   ApArgs a{};
   a.atom4 = p->d.atom4;
+  a.atom_lo = p->d.atom_lo;
   a.atom_w = p->d.atom_w;
   a.blocks = p->d.ap_blocks;
   a.coef = p->d.coef;
   a.n_s = p->n_s;
   a.s_hi = p->d.s_hi;
+  a.s_lo = p->d.s_lo;
+  a.axis_lo = p->d.axis_lo;
   a.axis_s = p->d.axis_s;
   a.n0 = p->n_axis[0];
   a.n1 = p->n_axis[1];

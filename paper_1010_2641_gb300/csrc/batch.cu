@@ -24,11 +24,13 @@ namespace scatter {
 
 struct BatchArgs {
   const float4* atom4;
+  const float4* atom_lo;  // position rounding errors (exact-product phases)
   const float* atom_w;
   const Segment* segs;
   const int32_t* chunk_seg_off;
   const float* coef;
   const float* s_hi;
+  const float* s_lo;  // rounding error of s_hi (double-float s of the exact-product phases)
   const double* S64;
   int64_t n_s;
   const BatchInst* inst;
@@ -49,6 +51,7 @@ struct BatchArgs {
 template <int R, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
   __shared__ __align__(128) float4 sh_atom[2][kTile];
+  __shared__ __align__(128) float4 sh_lo[2][kTile];
   __shared__ __align__(128) float sh_w[2][kTile];
   __shared__ __align__(8) uint64_t sh_bar[2];
   __shared__ int sh_item;
@@ -80,15 +83,25 @@ __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
     }
     const int chunk = in.chunk0 + w.chunk;
     float2 tot[R];
-    // batches take no factor table; a long crystal takes the exact-product phases
-    const bool ok =
-        dev::phase_needs_exact(a.inst_bbox + 6 * w.inst, a.inst_shift + 3 * w.inst, a.smax)
-            ? chunk_sum<kModeList, R, true>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
-                                            a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom,
-                                            sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0)
-            : chunk_sum<kModeList, R, false>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
-                                             a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sh_atom,
-                                             sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+    // batches take no factor table; a long crystal takes the exact-product
+    // phases with s as a double-float
+    bool ok;
+    if (dev::phase_needs_exact(a.inst_bbox + 6 * w.inst, a.inst_shift + 3 * w.inst, a.smax)) {
+      auto lo = [&](int r, float& x, float& y, float& z) {
+        const int64_t m = w.p0 + (int64_t)r * THREADS + tid;
+        const int64_t mm = valid[r] ? m : in.s_begin;
+        x = a.s_lo[mm];
+        y = a.s_lo[a.n_s + mm];
+        z = a.s_lo[2 * a.n_s + mm];
+      };
+      ok = chunk_sum_exact_halves<kModeList, R>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                                a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, lo,
+                                                sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+    } else {
+      ok = chunk_sum<kModeList, R, false>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                          a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sx, sy, sz,
+                                          sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+    }
     if (!ok) return;
     const int64_t M_b = in.s_end - in.s_begin;
     const double* t = a.inst_shift + 3 * w.inst;
@@ -283,11 +296,13 @@ scatter_status prepare_batch(scatter_plan_s* p) {
 scatter_status enqueue_batch_kernels(scatter_plan_t p, float2* amp, float* inten, cudaStream_t st) {
   BatchArgs a{};
   a.atom4 = p->d.atom4;
+  a.atom_lo = p->d.atom_lo;
   a.atom_w = p->d.atom_w;
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
   a.coef = p->d.coef;
   a.s_hi = p->d.s_hi;
+  a.s_lo = p->d.s_lo;
   a.S64 = p->d.S64;
   a.n_s = p->n_s;
   a.inst = p->d.batch_inst;

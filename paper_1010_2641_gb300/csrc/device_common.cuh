@@ -75,11 +75,26 @@ __device__ __forceinline__ float frac_product_plus(float a, float b, float acc) 
   return dev_frac_plus(p, fmaf(a, b, -p), acc);
 }
 
+// frac_product_plus for a double-float multiplier a + alo (alo the FP32
+// rounding error of a, |alo| <= ulp(a)/2): the low part's product joins the
+// rounding error.  Without it the multiplier's own rounding, |a| 2^-24 per
+// component, errs by that much times |b| cycles, coherently for one point.
+__device__ __forceinline__ float frac_product2_plus(float a, float alo, float b, float acc) {
+  const float p = a * b;
+  return dev_frac_plus(p, fmaf(alo, b, fmaf(a, b, -p)), acc);
+}
+
 // a b - rint(a b) with the product's rounding error restored (|result|
 // <= 1/2 + 2^-24 |a b|): the argument of the per-call tables' sincospif
 __device__ __forceinline__ float frac_of_product(float a, float b) {
   const float p = a * b;
   return (p - rintf(p)) + fmaf(a, b, -p);
+}
+
+// frac_of_product for a double-float multiplier a + alo
+__device__ __forceinline__ float frac_of_product2(float a, float alo, float b) {
+  const float p = a * b;
+  return (p - rintf(p)) + fmaf(alo, b, fmaf(a, b, -p));
 }
 
 // sin and cos of 2*pi*f for |f| <= 1/2 (cycles) on the MUFU pipe

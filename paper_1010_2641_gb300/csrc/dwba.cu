@@ -37,11 +37,13 @@ constexpr int kDwbaR = 4;          // alpha_f points per thread
 constexpr int kDwbaWarps = 8;      // 8 warps x 4 = 32 alpha_f per CTA
 constexpr int kDwbaThreads = 32 * kDwbaWarps;
 constexpr int kAfBlock = kDwbaR * kDwbaWarps;  // 32
-constexpr size_t kDwbaStageBytes = (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16 + kDwbaTile * 4;
+// stage: Z table tile, atom records, position rounding errors (exact instance), weights
+constexpr size_t kDwbaStageBytes = (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16 + kDwbaTile * 16 + kDwbaTile * 4;
 constexpr size_t kDwbaSmem = 2 * kDwbaStageBytes;
 
 struct DwbaArgs {
   const float4* atom4;
+  const float4* atom_lo;   // FP32 rounding errors of the positions (exact instance)
   const float* atom_w;
   const Segment* segs;
   const int32_t* chunk_seg_off;
@@ -49,6 +51,7 @@ struct DwbaArgs {
   const float4* ztab;      // [n_afb][n_slots][32] (Z1.re, Z1.im, Z2.re, Z2.im)
   int64_t n_slots;
   const float* axis_s;     // [n0 | n1 | n_af]: s_h, s_k (r.l.u. minus H), unused
+  const float* axis_lo;    // rounding errors of axis_s (double-float s of the exact phases)
   const double* axis64;    // [n0 | n1 | n_af]: h, k, alpha_f
   const float* gid_sz;     // [2][n_af] Sz1, Sz2 (r.l.u.)
   const double* gid_sz64;  // [2][n_af]
@@ -68,7 +71,8 @@ struct DwbaArgs {
 };
 
 // Z table of the call: Z1, Z2 for every slot and alpha_f (padded to 32).
-__global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float* __restrict__ sz, int64_t n_slots,
+__global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __restrict__ atom_lo,
+                              const float* __restrict__ sz, const float* __restrict__ sz_lo, int64_t n_slots,
                               int64_t n_af, int64_t n_afb, float4* __restrict__ ztab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = n_afb * n_slots * kAfBlock;
@@ -81,25 +85,35 @@ __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float* __r
     ztab[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  const float z = atom4[slot].z;
+  // Sz z with Sz and z as double-floats (the products' low parts are far
+  // below FP32 resolution unless the crystal is tall; they cost nothing here)
+  const float z = atom4[slot].z, ez = atom_lo[slot].z;
   float s1, c1, s2, c2;
-  sincospif(2.0f * dev::frac_of_product(sz[af], z), &s1, &c1);
-  sincospif(2.0f * dev::frac_of_product(sz[n_af + af], z), &s2, &c2);
+  sincospif(2.0f * (dev::frac_of_product2(sz[af], sz_lo[af], z) + sz[af] * ez), &s1, &c1);
+  sincospif(2.0f * (dev::frac_of_product2(sz[n_af + af], sz_lo[n_af + af], z) + sz[n_af + af] * ez), &s2, &c2);
   ztab[i] = make_float4(c1, s1, c2, s2);
 }
 
 // Tile sums of the four real products of E_j = w_j e^{2 pi i (s_h x'_j + s_k y'_j + c_j)}
 // with each Z of the thread's rows: [P, Q, R, T] of Z1, then of Z2.  EXACT: the
-// phase with its products' rounding errors restored (long crystals).
+// phase with its products' rounding errors restored and s_h, s_k as
+// double-floats (shl, skl their low parts; long crystals).
 template <bool EXACT>
-__device__ __forceinline__ void dwba_tile_products(const float4* zs, const float4* as, const float* ws, int cnt,
-                                                   int af_l0, float sh, float sk, float (&acc)[kDwbaR][8]) {
+__device__ __forceinline__ void dwba_tile_products(const float4* zs, const float4* as, const float4* es,
+                                                   const float* ws, int cnt, int af_l0, float sh, float sk, float shl,
+                                                   float skl, float (&acc)[kDwbaR][8]) {
 #pragma unroll 2
   for (int j = 0; j < cnt; ++j) {
     const float4 at = as[j];
     const float w = ws[j];
-    const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(sh, at.x, dev::frac_product_plus(sk, at.y, at.w)))
-                          : dev::frac_rn(fmaf(sk, at.y, fmaf(sh, at.x, at.w)));
+    float f;
+    if (EXACT) {
+      const float4 e = es[j];  // the positions' FP32 rounding errors
+      f = dev::frac_rn(dev::frac_product2_plus(
+          sh, shl, at.x, dev::frac_product2_plus(sk, skl, at.y, fmaf(sh, e.x, fmaf(sk, e.y, at.w)))));
+    } else {
+      f = dev::frac_rn(fmaf(sk, at.y, fmaf(sh, at.x, at.w)));
+    }
     float sn, cs;
     dev::sincos_cycles_mufu(f, &sn, &cs);
     const float er = w * cs, ei = w * sn;
@@ -133,6 +147,7 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
   const bool hk_ok = hk < a.n0 * a.n1;
   const int64_t i_h = hk_ok ? hk / a.n1 : 0, i_k = hk_ok ? hk % a.n1 : 0;
   const float sh = a.axis_s[i_h], sk = a.axis_s[a.n0 + i_k];
+  const float shl = EXACT ? a.axis_lo[i_h] : 0.f, skl = EXACT ? a.axis_lo[a.n0 + i_k] : 0.f;
   const int64_t afb = blockIdx.y;
   const int af_l0 = warp * kDwbaR;
   const int64_t af0 = afb * kAfBlock + af_l0;
@@ -142,8 +157,11 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
   auto stage_a = [&](int s) {
     return reinterpret_cast<float4*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16);
   };
+  auto stage_e = [&](int s) {
+    return reinterpret_cast<float4*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16);
+  };
   auto stage_w = [&](int s) {
-    return reinterpret_cast<float*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16);
+    return reinterpret_cast<float*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 32);
   };
 
   const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
@@ -160,9 +178,10 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
     if (l_seg >= seg_hi) return;
     const int64_t end = a.segs[l_seg].end;
     const int cnt = (int)dev::min64(kDwbaTile, end - l_begin);
-    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * (kAfBlock * 16u + 20u));
+    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * (kAfBlock * 16u + (EXACT ? 36u : 20u)));
     dev::bulk_g2s(stage_z(st), zbase + l_begin * kAfBlock, (uint32_t)cnt * kAfBlock * 16u, &sh_bar[st]);
     dev::bulk_g2s(stage_a(st), a.atom4 + l_begin, (uint32_t)cnt * 16u, &sh_bar[st]);
+    if (EXACT) dev::bulk_g2s(stage_e(st), a.atom_lo + l_begin, (uint32_t)cnt * 16u, &sh_bar[st]);
     dev::bulk_g2s(stage_w(st), a.atom_w + l_begin, (uint32_t)cnt * 4u, &sh_bar[st]);
     l_begin += cnt;
     if (l_begin >= end && ++l_seg < seg_hi) l_begin = a.segs[l_seg].begin;
@@ -195,7 +214,8 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     if (ok) {
-      dwba_tile_products<EXACT>(stage_z(st), stage_a(st), stage_w(st), cnt, af_l0, sh, sk, acc);
+      dwba_tile_products<EXACT>(stage_z(st), stage_a(st), stage_e(st), stage_w(st), cnt, af_l0, sh, sk, shl, skl,
+                                acc);
     }
     // beams of the tile: E Z1, E Z2, E conj(Z2), E conj(Z1)
 #pragma unroll
@@ -394,7 +414,7 @@ scatter_status prepare_gid(scatter_plan_s* p) {
   const double scale = p->lattice_a / p->wavelength;
   const std::complex<double> Ri = fresnel_r(p->alpha_i, p->delta, p->beta);
   std::vector<double> sz64(2 * n_af);
-  std::vector<float> sz(2 * n_af);
+  std::vector<float> sz(2 * n_af), sz_lo(2 * n_af);
   std::vector<double2> w64(4 * n_af);
   std::vector<float2> w32(4 * n_af);
   for (int64_t i = 0; i < n_af; ++i) {
@@ -408,8 +428,10 @@ scatter_status prepare_gid(scatter_plan_s* p) {
       w32[t * n_af + i] = make_float2((float)W[t].real(), (float)W[t].imag());
     }
     p->s_max[2] = std::max(p->s_max[2], std::fabs(sz64[i]));
-    sz[i] = (float)sz64[i];
-    sz[n_af + i] = (float)sz64[n_af + i];
+    for (int64_t q : {i, n_af + i}) {
+      sz[q] = (float)sz64[q];
+      sz_lo[q] = (float)(sz64[q] - (double)sz[q]);
+    }
   }
   cudaError_t e;
   auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
@@ -420,6 +442,8 @@ scatter_status prepare_gid(scatter_plan_s* p) {
   };
   p->gid_sz_host = sz64;
   if ((e = up((void**)&p->d.gid_sz, sz.data(), sz.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "gid");
+  if ((e = up((void**)&p->d.gid_sz_lo, sz_lo.data(), sz_lo.size() * sizeof(float))) != cudaSuccess)
+    return cuda_status(e, "gid");
   if ((e = up((void**)&p->d.gid_sz64, sz64.data(), sz64.size() * sizeof(double))) != cudaSuccess)
     return cuda_status(e, "gid");
   if ((e = up((void**)&p->d.gid_w, w32.data(), w32.size() * sizeof(float2))) != cudaSuccess) return cuda_status(e, "gid");
@@ -454,12 +478,14 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   const int64_t n_afb = (n_af + kAfBlock - 1) / kAfBlock;
   if (p->n_slots > 0) {
     const int64_t total = n_afb * p->n_slots * kAfBlock;
-    k_dwba_ztable<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p->d.atom4, p->d.gid_sz, p->n_slots, n_af, n_afb,
+    k_dwba_ztable<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p->d.atom4, p->d.atom_lo, p->d.gid_sz,
+                                                                    p->d.gid_sz_lo, p->n_slots, n_af, n_afb,
                                                                     p->d.ztab);
     p->last_launches += 1;
   }
   DwbaArgs a{};
   a.atom4 = p->d.atom4;
+  a.atom_lo = p->d.atom_lo;
   a.atom_w = p->d.atom_w;
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
@@ -467,6 +493,7 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   a.ztab = p->d.ztab;
   a.n_slots = p->n_slots;
   a.axis_s = p->d.axis_s;
+  a.axis_lo = p->d.axis_lo;
   a.axis64 = p->d.axis64;
   a.gid_sz = p->d.gid_sz;
   a.gid_sz64 = p->d.gid_sz64;

@@ -92,7 +92,7 @@ __global__ void k_prep(const double* __restrict__ xyz, const float* __restrict__
                        const int32_t* __restrict__ slot_src, const int32_t* __restrict__ slot_inst,
                        const int64_t* __restrict__ inst_slot_begin, const double* __restrict__ inst_H,
                        const unsigned long long* __restrict__ bbox, double* inst_shift, float4* atom4,
-                       float* atom_w, int64_t n_slots, unsigned* status) {
+                       float4* atom_lo, float* atom_w, int64_t n_slots, unsigned* status) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= n_slots) return;
   const int inst = slot_inst[slot];
@@ -109,6 +109,7 @@ __global__ void k_prep(const double* __restrict__ xyz, const float* __restrict__
   const int32_t src = slot_src[slot];
   if (src < 0) {
     atom4[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    atom_lo[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     atom_w[slot] = 0.f;
     return;
   }
@@ -128,11 +129,14 @@ __global__ void k_prep(const double* __restrict__ xyz, const float* __restrict__
   if (!ok) {
     dev::set_status(status, kStatusNonFinite);
     atom4[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    atom_lo[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     atom_w[slot] = 0.f;
     return;
   }
   c -= rint(c);
-  atom4[slot] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)c);
+  const float x0 = (float)r[0], x1 = (float)r[1], x2 = (float)r[2];
+  atom4[slot] = make_float4(x0, x1, x2, (float)c);
+  atom_lo[slot] = make_float4((float)(r[0] - (double)x0), (float)(r[1] - (double)x1), (float)(r[2] - (double)x2), 0.f);
   atom_w[slot] = w;
 }
 
@@ -143,6 +147,7 @@ __global__ void k_prep(const double* __restrict__ xyz, const float* __restrict__
 template <int MODE, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_generic(const GenericArgs a) {
   __shared__ __align__(128) float4 sh_atom[2][kTile];
+  __shared__ __align__(128) float4 sh_lo[2][kTile];  // position rounding errors (exact-product phases)
   __shared__ __align__(128) float sh_w[2][kTile];
   __shared__ __align__(8) uint64_t sh_bar[2];
 
@@ -195,14 +200,39 @@ __global__ void __launch_bounds__(THREADS) k_generic(const GenericArgs a) {
   float2 tot[R];
   int k = 0;
   // one decision per call (every CTA computes the same): phases that can
-  // pass kPhaseExactLim cycles take the exact-product route
-  const bool ok = dev::phase_needs_exact(a.bbox, a.shift, a.smax)
-                      ? chunk_sum<MODE, R, true>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
-                                                 a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz,
-                                                 sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride)
-                      : chunk_sum<MODE, R, false>(a.atom4, a.atom_w, a.segs, a.chunk_seg_off[chunk],
-                                                  a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz,
-                                                  sh_atom, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride);
+  // pass kPhaseExactLim cycles take the exact-product route, with s as a
+  // double-float
+  bool ok;
+  if (dev::phase_needs_exact(a.bbox, a.shift, a.smax_dev ? a.smax_dev : a.smax)) {
+    int64_t i0 = 0, i1 = 0, i2 = 0;
+    if (MODE == kModeGrid) {
+      const int64_t q = (a.n2 + R - 1) / R;
+      const int64_t g = (int64_t)blockIdx.x * THREADS + tid;
+      const int64_t line = g < a.n0 * a.n1 * q ? g / q : 0;
+      i0 = line / a.n1;
+      i1 = line % a.n1;
+      i2 = idx0 - line * a.n2;
+    }
+    auto lo = [&](int r, float& x, float& y, float& z) {
+      if (MODE == kModeGrid) {
+        x = a.axis_lo[i0];
+        y = a.axis_lo[a.n0 + i1];
+        z = a.axis_lo[a.n0 + a.n1 + dev::min64(i2 + r, a.n2 - 1)];
+      } else {
+        const int64_t m = valid[r] ? idx0 + (int64_t)r * THREADS + tid : 0;
+        x = a.s_lo[m];
+        y = a.s_lo[a.n_s + m];
+        z = a.s_lo[2 * a.n_s + m];
+      }
+    };
+    ok = chunk_sum_exact_halves<MODE, R>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                         a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz, lo, sh_atom,
+                                         sh_lo, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride);
+  } else {
+    ok = chunk_sum<MODE, R, false>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
+                                   a.chunk_seg_off[chunk + 1], a.coef, a.H, a.inv4a2, sx, sy, sz, sx, sy, sz, sh_atom,
+                                   sh_lo, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, pbase, pstride);
+  }
   if (!ok) return;
 
   // ---- epilogue -----------------------------------------------------------------
@@ -299,14 +329,17 @@ int mode_of(const scatter_plan_s* p) { return p->s_kind == SCATTER_S_GRID ? kMod
 GenericArgs make_args(scatter_plan_t p) {
   GenericArgs a{};
   a.atom4 = p->d.atom4;
+  a.atom_lo = p->d.atom_lo;
   a.atom_w = p->d.atom_w;
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
   a.coef = p->d.coef;
   a.n_s = p->n_s;
   a.s_hi = p->d.s_hi;
+  a.s_lo = p->d.s_lo;
   a.S64 = p->d.S64;
   a.axis_s = p->d.axis_s;
+  a.axis_lo = p->d.axis_lo;
   a.axis64 = p->d.axis64;
   a.n0 = p->n_axis[0];
   a.n1 = p->n_axis[1];
@@ -362,10 +395,17 @@ scatter_status launch_prep(scatter_plan_t p, const double* xyz, const float* occ
     const int64_t nb = (p->n_slots + 255) / 256;
     k_prep<<<(unsigned)nb, 256, 0, st>>>(xyz, occ, p->d.slot_src, p->d.slot_inst, p->d.inst_slot_begin,
                                          p->d.inst_H, p->d.inst_bbox, p->d.inst_shift, p->d.atom4,
-                                         p->d.atom_w, p->n_slots, p->d.status);
+                                         p->d.atom_lo, p->d.atom_w, p->n_slots, p->d.status);
     p->last_launches += 1;
   }
   return cuda_status(cudaGetLastError(), "prep launch");
+}
+
+scatter_status launch_bbox_raw(const double* xyz, const int64_t* atom_off, int batch, int64_t max_atoms,
+                               unsigned long long* bbox, unsigned* status, cudaStream_t st) {
+  const int bx = (int)dev::min64(std::max<int64_t>((max_atoms + 255) / 256, 1), 64);
+  k_bbox<<<dim3(bx, batch), 256, 0, st>>>(xyz, atom_off, bbox, status);
+  return cuda_status(cudaGetLastError(), "bounding-box launch");
 }
 
 scatter_status launch_generic_reduce(scatter_plan_t p, int n_chunks, float2* amp_out, float* int_out,

@@ -12,14 +12,17 @@ enum { kModeList = 0, kModeGrid = 1 };
 
 struct GenericArgs {
   const float4* atom4;
+  const float4* atom_lo;  // FP32 rounding errors of (x', y', z') (exact-product phases), 0
   const float* atom_w;
   const Segment* segs;
   const int32_t* chunk_seg_off;
   const float* coef;
   int64_t n_s;
   const float* s_hi;      // LIST [3][M]
+  const float* s_lo;      // LIST [3][M] FP32 rounding error of s_hi (exact-product phases)
   const double* S64;      // LIST [M][3]
   const float* axis_s;    // GRID [n0 | n1 | n2]
+  const float* axis_lo;   // GRID [n0 | n1 | n2] FP32 rounding error of axis_s
   const double* axis64;   // GRID [n0 | n1 | n2]
   int64_t n0, n1, n2;
   float H[3];
@@ -28,6 +31,7 @@ struct GenericArgs {
   const double* shift;    // [3] device, written by prep
   const unsigned long long* bbox;  // [6] device, this call's ordered min / max xyz (null: never exact)
   float smax[3];          // max |S_d - H_d| over the points
+  const float* smax_dev;  // the same maxima in device memory [3] (written by an earlier kernel), or null
   const float2* ftab;     // Eq. 4 factor table [n_species][M], or null (form factors)
   float2* out_amp;
   float* out_int;
@@ -46,18 +50,24 @@ scatter_status launch_generic_args(GenericArgs a, int R, int threads, int n_chun
 // Eq. 4 factor table, F_s(S) at the thread's point indices pbase + r pstride,
 // clamped to the map).  EXACT: crystals whose phases can pass
 // dev::kPhaseExactLim cycles take every product of the phase with its
-// rounding error restored.  `k` counts the
+// rounding error restored, with s as a double-float (s + lo: lx, ly, lz) and
+// the positions as double-floats (x' + e, e staged from atom_lo into sh_lo);
+// the lo parts are read only then.  A position rounded to FP32 errs by
+// |x'| 2^-24 cells, which at thousands of cells moves s.x' by ~1e-4 rad.  `k` counts the
 // tiles this CTA has consumed so far (it sets the stage and mbarrier parity
 // and carries over between chunks of a persistent CTA).  Returns false if a
 // wait gave up (the CTA then drains its copies and must stop).
 template <int MODE, int R, bool EXACT = false>
-__device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, const float* __restrict__ atom_w,
+__device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, const float4* __restrict__ atom_lo,
+                                          const float* __restrict__ atom_w,
                                           const Segment* __restrict__ segs, int seg_lo, int seg_hi,
                                           const float* __restrict__ coef, const float H[3], float inv4a2,
                                           const float (&sx)[R], const float (&sy)[R], const float (&sz)[R],
-                                          float4 (*sh_atom)[kTile], float (*sh_w)[kTile], uint64_t* sh_bar, int& k,
-                                          float2 (&tot)[R], unsigned* status, const float2* __restrict__ ftab,
-                                          int64_t n_s, int64_t pbase, int64_t pstride) {
+                                          const float (&lx)[R], const float (&ly)[R], const float (&lz)[R],
+                                          float4 (*sh_atom)[kTile], float4 (*sh_lo)[kTile], float (*sh_w)[kTile],
+                                          uint64_t* sh_bar, int& k, float2 (&tot)[R], unsigned* status,
+                                          const float2* __restrict__ ftab, int64_t n_s, int64_t pbase,
+                                          int64_t pstride) {
   const int tid = threadIdx.x;
   // loader state (used by thread 0 only)
   int l_seg = seg_lo;
@@ -66,9 +76,10 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
     if (l_seg >= seg_hi) return;
     const int64_t end = segs[l_seg].end;
     const int cnt = (int)dev::min64(kTile, end - l_begin);
-    dev::mbar_arrive_expect_tx(&sh_bar[stage], (uint32_t)cnt * 20u);
+    dev::mbar_arrive_expect_tx(&sh_bar[stage], (uint32_t)cnt * (EXACT ? 36u : 20u));
     dev::bulk_g2s(&sh_atom[stage][0], atom4 + l_begin, (uint32_t)cnt * 16u, &sh_bar[stage]);
     dev::bulk_g2s(&sh_w[stage][0], atom_w + l_begin, (uint32_t)cnt * 4u, &sh_bar[stage]);
+    if (EXACT) dev::bulk_g2s(&sh_lo[stage][0], atom_lo + l_begin, (uint32_t)cnt * 16u, &sh_bar[stage]);
     l_begin += cnt;
     if (l_begin >= end && ++l_seg < seg_hi) l_begin = segs[l_seg].begin;
   };
@@ -93,17 +104,22 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
     for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
     if (ok) {
       const float4* at4 = sh_atom[st];
+      const float4* atl = sh_lo[st];
       const float* atw = sh_w[st];
 #pragma unroll 2
       for (int j = 0; j < cnt; ++j) {
         const float4 at = at4[j];
+        const float4 e = EXACT ? atl[j] : at;  // position rounding errors (EXACT only)
         const float w = atw[j];
         if (MODE == kModeGrid) {
-          const float base = EXACT ? dev::frac_product_plus(sx[0], at.x, dev::frac_product_plus(sy[0], at.y, at.w))
-                                   : fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
+          const float base =
+              EXACT ? dev::frac_product2_plus(sx[0], lx[0], at.x,
+                                              dev::frac_product2_plus(sy[0], ly[0], at.y,
+                                                                      fmaf(sx[0], e.x, fmaf(sy[0], e.y, at.w))))
+                    : fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float f = EXACT ? dev::frac_rn(dev::frac_product_plus(sz[r], at.z, base))
+            const float f = EXACT ? dev::frac_rn(dev::frac_product2_plus(sz[r], lz[r], at.z, fmaf(sz[r], e.z, base)))
                                   : dev::frac_rn(fmaf(sz[r], at.z, base));
             float sn, cs;
             dev::sincos_cycles_mufu(f, &sn, &cs);
@@ -114,8 +130,12 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const float f =
-                EXACT ? dev::frac_rn(dev::frac_product_plus(
-                            sx[r], at.x, dev::frac_product_plus(sy[r], at.y, dev::frac_product_plus(sz[r], at.z, at.w))))
+                EXACT ? dev::frac_rn(dev::frac_product2_plus(
+                            sx[r], lx[r], at.x,
+                            dev::frac_product2_plus(
+                                sy[r], ly[r], at.y,
+                                dev::frac_product2_plus(sz[r], lz[r], at.z,
+                                                        fmaf(sx[r], e.x, fmaf(sy[r], e.y, fmaf(sz[r], e.z, at.w)))))))
                       : dev::frac_rn(fmaf(sz[r], at.z, fmaf(sy[r], at.y, fmaf(sx[r], at.x, at.w))));
             float sn, cs;
             dev::sincos_cycles_mufu(f, &sn, &cs);
@@ -158,6 +178,48 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
     }
     if (tid == 0) issue(st);
     ++k;
+  }
+  return true;
+}
+
+// The exact-product sum of chunk_sum for R points, run as two passes of R/2
+// points over the chunk's atoms.  The exact phases need the low parts of s
+// besides everything the plain loop holds; halving the points per pass keeps
+// the exact branch within the registers of the plain one, so the plain
+// loop, the one that runs on common maps, keeps its register allocation.
+// lo(r, &x, &y, &z) yields the low parts of point r.  Returns false if a
+// wait gave up.
+template <int MODE, int R, class LoFn>
+__device__ __forceinline__ bool chunk_sum_exact_halves(
+    const float4* __restrict__ atom4, const float4* __restrict__ atom_lo, const float* __restrict__ atom_w,
+    const Segment* __restrict__ segs,
+    int seg_lo, int seg_hi, const float* __restrict__ coef, const float H[3], float inv4a2, const float (&sx)[R],
+    const float (&sy)[R], const float (&sz)[R], LoFn lo, float4 (*sh_atom)[kTile], float4 (*sh_lo)[kTile],
+    float (*sh_w)[kTile], uint64_t* sh_bar, int& k, float2 (&tot)[R], unsigned* status, const float2* __restrict__ ftab, int64_t n_s,
+    int64_t pbase, int64_t pstride) {
+  static_assert(R % 2 == 0, "two halves of the thread's points");
+  constexpr int R2 = R / 2;
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    float hx[R2], hy[R2], hz[R2], lx[R2], ly[R2], lz[R2];
+    float2 t2[R2];
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+      const int q = half * R2 + r;
+      hx[r] = sx[q];
+      hy[r] = sy[q];
+      hz[r] = sz[q];
+      lo(q, lx[r], ly[r], lz[r]);
+    }
+    if (!chunk_sum<MODE, R2, true>(atom4, atom_lo, atom_w, segs, seg_lo, seg_hi, coef, H, inv4a2, hx, hy, hz, lx,
+                                   ly, lz, sh_atom, sh_lo, sh_w, sh_bar, k, t2, status, ftab, n_s,
+                                   pbase + half * R2 * pstride, pstride))
+      return false;
+    // the next pass re-stages the chunk's tiles: every thread is done with
+    // the shared stages of this one
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R2; ++r) tot[half * R2 + r] = t2[r];
   }
   return true;
 }

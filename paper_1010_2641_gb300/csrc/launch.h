@@ -10,6 +10,13 @@ namespace scatter {
 // c = frac(H . delta), fp32 slots.  Enqueued on `st`.
 scatter_status launch_prep(scatter_plan_t p, const double* xyz, const float* occ, cudaStream_t st);
 
+// Bounding boxes of `batch` instances (ordered-int min / max xyz, atom ranges
+// atom_off [batch+1] in device memory) into `bbox` [batch][6], which must hold
+// the empty-box values (min slots ~0, max slots 0) beforehand; non-finite
+// coordinates set kStatusNonFinite.  For callers that own their buffers.
+scatter_status launch_bbox_raw(const double* xyz, const int64_t* atom_off, int batch, int64_t max_atoms,
+                               unsigned long long* bbox, unsigned* status, cudaStream_t st);
+
 // A(S) (and/or |A|^2) of every point with the generic FP32/MUFU kernel;
 // positions must have been prepared by launch_prep on the same stream.
 scatter_status launch_generic(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);

@@ -218,6 +218,7 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.slot_src);
   release(d.slot_inst);
   release(d.atom4);
+  release(d.atom_lo);
   release(d.atom_w);
   release(d.atom_species);
   release(d.segs);
@@ -230,9 +231,11 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.inst_shift);
   release(d.inst_bbox);
   release(d.s_hi);
+  release(d.s_lo);
   release(d.S64);
   release(d.s_inst);
   release(d.axis_s);
+  release(d.axis_lo);
   release(d.axis64);
   release(d.partial);
   release(d.amp);
@@ -240,6 +243,7 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.gS);
   release(d.status);
   release(d.gid_sz);
+  release(d.gid_sz_lo);
   release(d.gid_sz64);
   release(d.gid_w);
   release(d.gid_w64);
@@ -251,6 +255,7 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.ftab);
   release(d.ftab64);
   release(d.sep_axis_s);
+  release(d.sep_axis_lo);
   release(d.sep_axis64);
   release(d.sep_virt);
   release(d.batch_inst);
@@ -393,6 +398,7 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   if ((st = upload(&d.slot_src, slot_src.data(), slot_src.size(), &bytes))) return st;
   if ((st = upload(&d.slot_inst, slot_inst.data(), slot_inst.size(), &bytes))) return st;
   if ((st = upload<float4>(&d.atom4, nullptr, slot_src.size(), &bytes))) return st;
+  if ((st = upload<float4>(&d.atom_lo, nullptr, slot_src.size(), &bytes))) return st;
   if ((st = upload<float>(&d.atom_w, nullptr, slot_src.size(), &bytes))) return st;
   if ((st = upload(&d.atom_species, species_caller.data(), species_caller.size(), &bytes))) return st;
   if ((st = upload(&d.coef, coef32.data(), coef32.size(), &bytes))) return st;
@@ -407,20 +413,26 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   if ((e = cudaMemset(d.status, 0, sizeof(unsigned))) != cudaSuccess) return cuda_status(e, "memset");
   if (p->n_slots > 0) {
     if ((e = cudaMemset(d.atom4, 0, sizeof(float4) * p->n_slots)) != cudaSuccess) return cuda_status(e, "memset");
+    if ((e = cudaMemset(d.atom_lo, 0, sizeof(float4) * p->n_slots)) != cudaSuccess) return cuda_status(e, "memset");
     if ((e = cudaMemset(d.atom_w, 0, sizeof(float) * p->n_slots)) != cudaSuccess) return cuda_status(e, "memset");
   }
 
   if (pr->s_kind == SCATTER_S_LIST) {
     const int64_t M = p->n_s;
-    std::vector<float> s_hi(3 * (size_t)M);
+    std::vector<float> s_hi(3 * (size_t)M), s_lo(3 * (size_t)M);
     for (int b = 0; b < B; ++b) {
       const Instance& in = p->inst[b];
       for (int64_t m = in.s_begin; m < in.s_end; ++m)
-        for (int dd = 0; dd < 3; ++dd) s_hi[(size_t)dd * M + m] = (float)(pr->s_list[3 * m + dd] - in.H[dd]);
+        for (int dd = 0; dd < 3; ++dd) {
+          const double sv = pr->s_list[3 * m + dd] - in.H[dd];
+          s_hi[(size_t)dd * M + m] = (float)sv;
+          s_lo[(size_t)dd * M + m] = (float)(sv - (double)(float)sv);
+        }
     }
     for (int64_t m = 0; m < M; ++m)
       for (int dd = 0; dd < 3; ++dd) p->s_max[dd] = std::max(p->s_max[dd], (double)std::fabs(s_hi[(size_t)dd * M + m]));
     if ((st = upload(&d.s_hi, s_hi.data(), s_hi.size(), &bytes))) return st;
+    if ((st = upload(&d.s_lo, s_lo.data(), s_lo.size(), &bytes))) return st;
     if ((st = upload(&d.S64, pr->s_list, 3 * (size_t)M, &bytes))) return st;
     if (B > 1) {
       std::vector<int32_t> s_inst(M);
@@ -429,16 +441,19 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
       if ((st = upload(&d.s_inst, s_inst.data(), s_inst.size(), &bytes))) return st;
     }
   } else {
-    std::vector<float> ax;
+    std::vector<float> ax, ax_lo;
     std::vector<double> ax64;
     for (int dd = 0; dd < 3; ++dd)
       for (int64_t i = 0; i < pr->n_axis[dd]; ++i) {
         ax64.push_back(pr->axis[dd][i]);
-        ax.push_back((float)(pr->axis[dd][i] - p->inst[0].H[dd]));
+        const double sv = pr->axis[dd][i] - p->inst[0].H[dd];
+        ax.push_back((float)sv);
+        ax_lo.push_back((float)(sv - (double)(float)sv));
         if (pr->s_kind == SCATTER_S_GRID || dd < 2)
           p->s_max[dd] = std::max(p->s_max[dd], std::fabs(pr->axis[dd][i] - p->inst[0].H[dd]));
       }
     if ((st = upload(&d.axis_s, ax.data(), ax.size(), &bytes))) return st;
+    if ((st = upload(&d.axis_lo, ax_lo.data(), ax_lo.size(), &bytes))) return st;
     if ((st = upload(&d.axis64, ax64.data(), ax64.size(), &bytes))) return st;
   }
   // Eq. 4 factor table (block structure factors), FP32 and FP64 copies

@@ -8,9 +8,13 @@
 //            atom4[slot]     (x', y', z', c) fp32: x' = r - t (lattice units,
 //                            t the per-call integer centring of the instance),
 //                            c = frac(H . delta) with delta = r - t - rint(r - t)
+//            atom_lo[slot]   (x, y, z) - fp32(x', y', z'), 0: the positions as
+//                            double-floats for the exact-product phases
 //            atom_w[slot]    occupancy (0 for padding)
-//   S      : LIST  -> s_hi[3][M] fp32 (s = S - H), S64[M][3] fp64 (epilogue)
-//            GRID  -> axis_s[d][n_d] fp32, axis64[d][n_d] fp64
+//   S      : LIST  -> s_hi[3][M] fp32 (s = S - H), s_lo[3][M] its rounding
+//                     error, S64[M][3] fp64 (epilogue)
+//            GRID  -> axis_s[d][n_d] fp32, axis_lo[d][n_d] its rounding
+//                     error, axis64[d][n_d] fp64
 //   chunks : split-K partition of each instance's slots into contiguous
 //            pieces; a chunk is a list of segments (slot range, species).
 #pragma once
@@ -81,6 +85,7 @@ struct DeviceBuffers {
   int32_t* slot_src = nullptr;      // [n_slots]
   int32_t* slot_inst = nullptr;     // [n_slots]
   float4* atom4 = nullptr;          // [n_slots]
+  float4* atom_lo = nullptr;        // [n_slots] FP32 rounding errors of (x', y', z'), 0
   float* atom_w = nullptr;          // [n_slots]
   int32_t* atom_species = nullptr;  // [n_atoms] caller order (FP64 kernel)
   Segment* segs = nullptr;          // [n_segs] (chunked)
@@ -94,9 +99,11 @@ struct DeviceBuffers {
   unsigned long long* inst_bbox = nullptr;  // [batch][6] ordered-int min/max
   // S
   float* s_hi = nullptr;            // LIST: [3][M]
+  float* s_lo = nullptr;            // LIST: [3][M] s - s_hi (double-float s of the exact-product phases)
   double* S64 = nullptr;            // LIST: [M][3]
   int32_t* s_inst = nullptr;        // LIST batch: instance of each point (or null)
   float* axis_s = nullptr;          // GRID: concatenated axes (s = axis - H)
+  float* axis_lo = nullptr;         // GRID: s - axis_s
   double* axis64 = nullptr;         // GRID: concatenated axes (full S)
   // workspace
   float2* partial = nullptr;        // [split_k][M] split-K partials
@@ -106,6 +113,7 @@ struct DeviceBuffers {
   unsigned* status = nullptr;       // [1]
   // grazing incidence (GID grids)
   float* gid_sz = nullptr;          // [2][n_af] Sz1, Sz2 r.l.u.
+  float* gid_sz_lo = nullptr;       // [2][n_af] their FP32 rounding errors
   double* gid_sz64 = nullptr;       // [2][n_af]
   float2* gid_w = nullptr;          // [4][n_af] beam weights
   double2* gid_w64 = nullptr;       // [4][n_af]
@@ -118,6 +126,7 @@ struct DeviceBuffers {
   float2* ftab = nullptr;           // Eq. 4 factor table [n_species][M], or null (form factors)
   double* ftab64 = nullptr;         // the same in FP64 (re, im) for the FP64 kernel
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
+  float* sep_axis_lo = nullptr;     // their FP32 rounding errors
   double* sep_axis64 = nullptr;     // separable grid axes, full S
   float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid
   // batches

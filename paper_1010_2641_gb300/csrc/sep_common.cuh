@@ -97,6 +97,7 @@ struct SepArgs {
   const Segment* ntiles;  // adjoint: slot range and species of each N tile; null: N = grid points
   const float4* atom4;    // adjoint: the columns' atoms (y', z' read)
   const float* axis_s;    // forward: the columns' points, s = axis - H ([n0 | n1 | n2])
+  const float* axis_lo;   // forward: rounding errors of axis_s (double-float s, exact formation); adjoint null
   const unsigned long long* bbox;  // instance 0: ordered min xyz, max xyz of this call's positions
   const double* shift;             // instance 0: its centring t
   float smax_b, smax_c;            // max |s| of the b and c axes

@@ -57,8 +57,10 @@ namespace scatter {
 
 struct SepTabArgs {
   const float4* atom4;
+  const float4* atom_lo;  // position rounding errors
   const float* atom_w;
   const float* axis_s;  // [n0 | n1 | n2] s values
+  const float* axis_lo; // their FP32 rounding errors (s as a double-float)
   int64_t n0, n1, n2;
   int64_t n_slots, n_steps, n_mt;
   uint4* A;             // [n_mt/2][n_steps][2 tiles][hi|lo][4 kb][16 mg][8 rows] of 16 B
@@ -76,13 +78,13 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
   const int64_t a = m >> 1;
   const int ri = (int)(m & 1);
   float v[8];
-  const float sa = a < t.n0 ? t.axis_s[a] : 0.f;
+  const float sa = a < t.n0 ? t.axis_s[a] : 0.f, sal = a < t.n0 ? t.axis_lo[a] : 0.f;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int64_t slot = ks * kSepStep + kb * 4 + q;
     float sn = 0.f, cs = 0.f;
     if (a < t.n0) {
-      sincospif(2.0f * dev::frac_of_product(sa, t.atom4[slot].x), &sn, &cs);
+      sincospif(2.0f * (dev::frac_of_product2(sa, sal, t.atom4[slot].x) + sa * t.atom_lo[slot].x), &sn, &cs);
       const float w = t.atom_w[slot];
       sn *= w;
       cs *= w;
@@ -285,7 +287,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     // offsets (s_b, s_c) from H, adjoint the atom's (y', z')
     const int64_t col = col_base + tid;
     const bool row_ok = col < col_end;
-    float sb, sc;
+    float sb, sc, sbl = 0.f, scl = 0.f;  // sbl, scl: low parts of a double-float s (forward)
     if (a.ntiles) {
       const float4 at = row_ok ? a.atom4[col] : make_float4(0.f, 0.f, 0.f, 0.f);
       sb = at.y;
@@ -294,6 +296,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       const int64_t rb = row_ok ? col / a.n2 : 0, rc = row_ok ? col % a.n2 : 0;
       sb = a.axis_s[a.n0 + rb];
       sc = a.axis_s[a.n0 + a.n1 + rc];
+      if (a.axis_lo) {
+        sbl = a.axis_lo[a.n0 + rb];
+        scl = a.axis_lo[a.n0 + a.n1 + rc];
+      }
     }
     const uint32_t b_row_off = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
     // |s_b y' + s_c z' + c| of every B element of this call stays below
@@ -344,7 +350,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
             for (int q = 0; q < 4; ++q) {
               const float4 v = at[kb * 4 + q];
               const float ph =
-                  kMode == 2 ? dev::frac_rn(dev::frac_product_plus(sb, v.y, dev::frac_product_plus(sc, v.z, v.w)))
+                  kMode == 2 ? dev::frac_rn(dev::frac_product2_plus(sb, sbl, v.y,
+                                                                    dev::frac_product2_plus(sc, scl, v.z, v.w)))
                   : kMode == 1 ? dev::frac_rn(fmaf(sb, v.y, fmaf(sc, v.z, v.w)))
                                : fmaf(sb, v.y, fmaf(sc, v.z, v.w));
               float sn, cs;
@@ -552,12 +559,14 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     ax64[2] = p->axis_host[2];
   }
   std::vector<double> all64;
-  std::vector<float> alls;
+  std::vector<float> alls, alls_lo;
   for (int d = 0; d < 3; ++d) {
     p->sep_n[d] = (int64_t)ax64[d].size();
     for (double v : ax64[d]) {
       all64.push_back(v);
-      alls.push_back((float)(v - p->inst[0].H[d]));
+      const double sv = v - p->inst[0].H[d];
+      alls.push_back((float)sv);
+      alls_lo.push_back((float)(sv - (double)(float)sv));
     }
   }
   p->sep_ns = p->sep_n[0] * p->sep_n[1] * p->sep_n[2];
@@ -611,8 +620,10 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   if ((e = cudaMalloc(&p->d.sep_chunks, chunk_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc chunks");
   cudaMemcpy(p->d.sep_chunks, chunks.data(), chunk_bytes, cudaMemcpyHostToDevice);
   if ((e = cudaMalloc(&p->d.sep_axis_s, alls.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
+  if ((e = cudaMalloc(&p->d.sep_axis_lo, alls_lo.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
   if ((e = cudaMalloc(&p->d.sep_axis64, all64.size() * sizeof(double))) != cudaSuccess) return cuda_status(e, "axes");
   cudaMemcpy(p->d.sep_axis_s, alls.data(), alls.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d.sep_axis_lo, alls_lo.data(), alls_lo.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d.sep_axis64, all64.data(), all64.size() * sizeof(double), cudaMemcpyHostToDevice);
   size_t virt_bytes = 0;
   if (gid) {
@@ -627,8 +638,10 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
 scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st) {
   SepTabArgs t{};
   t.atom4 = p->d.atom4;
+  t.atom_lo = p->d.atom_lo;
   t.atom_w = p->d.atom_w;
   t.axis_s = p->d.sep_axis_s;
+  t.axis_lo = p->d.sep_axis_lo;
   t.n0 = p->sep_n[0];
   t.n1 = p->sep_n[1];
   t.n2 = p->sep_n[2];
@@ -653,6 +666,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.smax_b = p->sep_smax[0];
   a.smax_c = p->sep_smax[1];
   a.axis_s = p->d.sep_axis_s;
+  a.axis_lo = p->d.sep_axis_lo;
   a.n0 = p->sep_n[0];
   a.n1 = p->sep_n[1];
   a.n2 = p->sep_n[2];

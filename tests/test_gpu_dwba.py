@@ -118,7 +118,7 @@ def test_ge_dot_map_sampled(path, tol):
     assert rel_l2(A[idx], ref) < tol
 
 
-@pytest.mark.parametrize("path,tol", [("generic", 1e-3), ("separable", 1e-3)])
+@pytest.mark.parametrize("path,tol", [("generic", 1e-4), ("separable", 1e-3)])
 def test_long_chain_takes_exact_phases(path, tol):
     """A 20,000-atom in-plane chain (displaced by N(0, 0.02) cells) with h
     within +-0.1 of the reference reflection: |s_h x'| reaches ~1000 cycles,

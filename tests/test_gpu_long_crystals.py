@@ -1,10 +1,12 @@
 """Long crystals on the S-list kernels: a displaced 20,000-atom chain along x
 with reflections within +-0.1 r.l.u. of (400) makes phases of ~1000 cycles,
 above the 128 cycles from which every FP32 kernel takes each phase product
-with its rounding error restored.  These cases run the exact branches of
-the generic list kernel, the atom-parallel kernel and the batched
-persistent kernel (an uneven batch whose first instance is the chain),
-against the FP64 oracle."""
+with its rounding error restored and s = S - H as a double-float (its FP32
+rounding alone, |s| 2^-24 per component times 1e4 cells, errs by ~1e-4 of the
+map).  These cases run the exact branches of the generic list kernel, the
+atom-parallel kernel and the batched persistent kernel (an uneven batch
+whose first instance is the chain), against the FP64 oracle at the FP32
+paths' 1e-4."""
 import numpy as np
 import pytest
 import torch
@@ -59,7 +61,7 @@ def test_chain_on_list_kernels(atoms_per_thread):
     assert plan.info()["atoms_per_thread"] == atoms_per_thread
     err = rel_l2(run(plan, xyz), oracle.amplitude(xyz, S, coef, A_LAT, species=sp))
     print(f"long chain, list, atoms_per_thread={atoms_per_thread}: rel L2 {err:.1e}")
-    assert err < 1e-3
+    assert err < 1e-4
 
 
 def test_chain_in_a_batch():
@@ -76,7 +78,7 @@ def test_chain_in_a_batch():
     err0 = rel_l2(A[:len(S0)], oracle.amplitude(xyz0, S0, coef, A_LAT, species=sp0))
     err1 = rel_l2(A[len(S0):], oracle.amplitude(c.xyz, S1, coef, A_LAT, species=sp[N_CHAIN:]))
     print(f"batch: long chain rel L2 {err0:.1e}, sphere {err1:.1e}")
-    assert err0 < 1e-3
+    assert err0 < 1e-4
     assert err1 < 1e-4
 
 
