@@ -388,12 +388,15 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
-def _time_calls(fn, plan, reps=2):
+def _time_calls(fn, plan, reps=2, min_s=0.0):
+    """Mean main-kernel time (plan events) of at least `reps` calls after one
+    warm-up call, repeated until `min_s` seconds have passed (up to 2000 calls)."""
     import torch
     fn()
     torch.cuda.synchronize()
     ms = []
-    for _ in range(reps):
+    t0 = time.time()
+    while len(ms) < reps or (time.time() - t0 < min_s and len(ms) < 2000):
         fn()
         ms.append(plan.timing()[0])
     return float(np.mean(ms))
@@ -407,10 +410,11 @@ def _rate_roof(units, ms, per_sm_clk, n_sm, clk, unit, bound, basis):
     peak = n_sm * per_sm_clk * clk["sm_mhz"] * 1e6
     achieved = units / (ms * 1e-3)
     return {"bound": bound, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": unit, "frac": achieved / peak,
-            "peak_basis": f"{n_sm} SMs x {per_sm_clk:g} {basis}/SM/clk x {clk['sm_mhz']:.0f} MHz (median sampled)"}
+            "peak_basis": f"{n_sm} SMs x {per_sm_clk:g} {basis}/SM/clk x {clk['sm_mhz']:.0f} MHz (median sampled)",
+            "clocks": clk}
 
 
-def _tensor_roof(n0, n12, n_atoms_padded, ms):
+def _tensor_roof(n0, n12, n_atoms_padded, ms, clk=None):
     """Executed-flop roofline of k_sep on an n0 x n12 separable grid."""
     m_pad = -(-2 * n0 // 128) * 128
     n_pad = -(-n12 // 256) * 256
@@ -418,10 +422,10 @@ def _tensor_roof(n0, n12, n_atoms_padded, ms):
     peak, basis = measured_peak("bf16_tflops", 1900.0)
     achieved = executed / (ms * 1e-3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)", "clocks": clk}
 
 
-def _tensor_roof_adjoint(n0, n12, n_atoms_padded, ms):
+def _tensor_roof_adjoint(n0, n12, n_atoms_padded, ms, clk=None):
     """Executed-flop roofline of k_sep running the adjoint: rows (a, weight,
     Re/Im) = 6 n0, columns = atom slots in 256-slot tiles, K = 2 per point."""
     m_pad = -(-6 * n0 // 128) * 128
@@ -431,7 +435,7 @@ def _tensor_roof_adjoint(n0, n12, n_atoms_padded, ms):
     peak, basis = measured_peak("bf16_tflops", 1900.0)
     achieved = executed / (ms * 1e-3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
+            "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)", "clocks": clk}
 
 
 def _time_whole(fn, reps=3):
@@ -457,6 +461,18 @@ def measure_paths(args, dev, clk, only=None):
     from paper_1010_2641_gb300 import api
     from paper_1010_2641_gb300 import workloads as W
     res = {}
+    rc = {}
+
+    def timed(fn, plan, reps=2):
+        """_time_calls over at least 0.5 s, with the SM clocks sampled while
+        the calls ran kept in rc["clk"]: each row's roofline takes the clock
+        its own kernel ran at."""
+        cs = ClockSampler(0, args.log_dir)
+        cs.start()
+        ms = _time_calls(fn, plan, reps, min_s=0.5)
+        rc["clk"] = cs.stop()
+        return ms
+
     c, axes = workload()
     xyz = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
     n_atoms, n_s = len(c.xyz), GRID[0] * GRID[1] * GRID[2]
@@ -470,22 +486,34 @@ def measure_paths(args, dev, clk, only=None):
         # generic FP32/MUFU kernel on the full strained-sphere map, with its roofline
         other = "generic" if args.path == "separable" else "separable"
         plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, path=other, timing=True)
-        ms = _time_calls(lambda: plan.amplitude(xyz), plan)
+        ms = timed(lambda: plan.amplitude(xyz), plan)
         row = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "workload": "strained sphere, full map"}
         n_sm = plan.info()["n_sm"]
         if other == "generic":
-            row["roofline"] = _rate_roof(n_atoms * n_s, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+            row["roofline"] = _rate_roof(n_atoms * n_s, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, rc.get("clk"),
                                          "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")
         else:
-            row["roofline"] = _tensor_roof(GRID[0], GRID[1] * GRID[2], plan.info()["n_atoms_padded"], ms)
+            row["roofline"] = _tensor_roof(GRID[0], GRID[1] * GRID[2], plan.info()["n_atoms_padded"], ms,
+                                            rc.get("clk"))
         res[f"{other}_sphere"] = row
         del plan
+    if want("auto_sphere"):
+        # the same map with default options: the plan picks the path itself
+        plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, timing=True)
+        xa = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
+        ms = timed(lambda: plan.amplitude(xa), plan)
+        inf = plan.info()
+        res["auto_sphere"] = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                              "path_chosen": {1: "generic", 2: "separable"}.get(inf["path"], str(inf["path"])),
+                              "workload": "strained sphere, full map, default options (AUTO, tolerance 1e-4)",
+                              "clocks": rc.get("clk")}
+        del plan, xa
     if want('fp64_sphere_slice'):
         # plain FP64 kernel on a 1/16 slice of the same map (every 16th l plane)
         sub = [axes[0], axes[1], axes[2][::16]]
         n_sub = len(sub[0]) * len(sub[1]) * len(sub[2])
         plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=sub, atom_species=c.species, path="fp64", timing=True)
-        ms = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
+        ms = timed(lambda: plan.amplitude(xyz), plan, reps=1)
         res["fp64_sphere_slice"] = {"value": n_atoms * n_sub / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "n_s": n_sub}
         del plan, xyz
     if want('fft_sphere_approx'):
@@ -506,7 +534,7 @@ def measure_paths(args, dev, clk, only=None):
         max_qu, outside = fp.validity()
         plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=fp.axes(), atom_species=c.species, path="separable",
                         timing=True)
-        ms_dir = _time_calls(lambda: plan.amplitude(xyz), plan, reps=1)
+        ms_dir = timed(lambda: plan.amplitude(xyz), plan, reps=1)
         A_dir = plan.amplitude(xyz).reshape(A_fft.shape)
         err = (torch.linalg.vector_norm(A_fft - A_dir) / torch.linalg.vector_norm(A_dir)).item()
         # the same near H: |q_d| <= 0.1 r.l.u. (12 bins of 1/128 r.l.u. each side), where |q.u| is 10x smaller
@@ -526,17 +554,17 @@ def measure_paths(args, dev, clk, only=None):
         cube = W.strained_cube()
         ax = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
               W.linspace_axis(4.0, 128, step=0.005)]
-        plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, timing=True)
+        plan = api.Plan(cube.coef, W.LATTICE_A, len(cube.xyz), axes=ax, timing=True, path="generic")
         x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
         I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
         A = plan.amplitude(x)
-        ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
-        ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
+        ms_f = timed(lambda: plan.amplitude(x, out=A), plan)
+        ms = timed(lambda: plan.backward(x, A, I_obs), plan)
         res["adjoint_cube"] = {"value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
                                "forward_kernel_ms": ms_f, "workload": "strained cube 102400 atoms x 128^3, dL/dr",
                                # uniform l axis: the line kernel carries the phase along l by a complex multiply,
                                # 8 FMA-pipe ops per pair at 128 lane-ops per SM per clock, no MUFU
-                               "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, clk, "Gpair/s", "alu",
+                               "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, rc.get("clk"), "Gpair/s", "alu",
                                                       "pairs (8 FMA-pipe ops each)")}
         del plan, x, A, I_obs
     if want('adjoint_cube_separable'):
@@ -548,15 +576,16 @@ def measure_paths(args, dev, clk, only=None):
         x = torch.tensor(cube.xyz, dtype=torch.float64, device=dev)
         I_obs = plan.intensity(torch.tensor(W.perturbed_copy(cube).xyz, dtype=torch.float64, device=dev))
         A = plan.amplitude(x)
-        ms_f = _time_calls(lambda: plan.amplitude(x, out=A), plan)
-        ms = _time_calls(lambda: plan.backward(x, A, I_obs), plan)
+        ms_f = timed(lambda: plan.amplitude(x, out=A), plan)
+        ms = timed(lambda: plan.backward(x, A, I_obs), plan)
         ms_call = _time_whole(lambda: plan.backward(x, A, I_obs))
         assert plan.info()["adjoint_form"] == 3
         res["adjoint_cube_separable"] = {
             "value": len(cube.xyz) * 128 ** 3 / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "call_ms": ms_call,
             "call_value": len(cube.xyz) * 128 ** 3 / (ms_call * 1e-3), "forward_kernel_ms": ms_f,
             "workload": "strained cube 102400 atoms x 128^3, dL/dr on a SEPARABLE plan (k_sep, operands swapped)",
-            "roofline": _tensor_roof_adjoint(128, 128 * 128, plan.info()["n_atoms_padded"], ms)}
+            "roofline": _tensor_roof_adjoint(128, 128 * 128, plan.info()["n_atoms_padded"], ms,
+                                                 rc.get("clk"))}
         del plan, x, A, I_obs
     if only == 'dwba_island_mid':
         # profiling case of the FFMA DWBA kernel: 127,560-atom island (base 60, height 20 cells) x 128x128x32
@@ -565,7 +594,7 @@ def measure_paths(args, dev, clk, only=None):
         plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes(128, 128, 32)),
                         atom_species=isl.species, gid=gid, path="generic", timing=True)
         x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
-        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=2)
+        ms = timed(lambda: plan.amplitude(x), plan, reps=2)
         res["dwba_island_mid"] = {"value": 4 * len(isl.xyz) * 128 * 128 * 32 / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
                                   "kernel_ms": ms, "workload": f"island {len(isl.xyz)} atoms x 128x128x32, FFMA kernel"}
         del plan, x
@@ -574,24 +603,25 @@ def measure_paths(args, dev, clk, only=None):
         isl = W.truncated_pyramid()
         gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
         plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
-                        gid=gid, timing=True)
+                        gid=gid, timing=True, path="generic")
         x = torch.tensor(isl.xyz, dtype=torch.float64, device=dev)
-        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+        ms = timed(lambda: plan.amplitude(x), plan, reps=1)
         m_gid = 512 * 512 * 32
         res["dwba_island"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
                               "kernel_ms": ms, "workload": "island 1013496 atoms x 512x512x32, 4 beams, FFMA kernel",
                               # 8 FFMA per (atom, point) for the four beams (they share the real products of
                               # E and Z1, Z2): 16 points = 64 beam-pairs per SM per clock on the FMA pipe
-                              "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 64.0, n_sm, clk, "Gbeam-pair/s",
+                              "roofline": _rate_roof(4 * len(isl.xyz) * m_gid, ms, 64.0, n_sm, rc.get("clk"), "Gbeam-pair/s",
                                                      "alu", "beam-pairs (8 FFMA per atom-point, 128 FFMA/SM/clk)")}
         del plan
         plan = api.Plan(isl.coef, W.LATTICE_A, len(isl.xyz), axes=list(W.gid_axes()), atom_species=isl.species,
                         gid=gid, path="separable", timing=True)
-        ms = _time_calls(lambda: plan.amplitude(x), plan, reps=1)
+        ms = timed(lambda: plan.amplitude(x), plan, reps=1)
         res["dwba_island_separable"] = {"value": 4 * len(isl.xyz) * m_gid / (ms * 1e-3), "unit": UNIT + " (x4 beams)",
                                         "kernel_ms": ms,
                                         "workload": "same map, beams stacked on a virtual l axis, tensor cores",
-                                        "roofline": _tensor_roof(512, 512 * 4 * 32, plan.info()["n_atoms_padded"], ms)}
+                                        "roofline": _tensor_roof(512, 512 * 4 * 32, plan.info()["n_atoms_padded"], ms,
+                                                                 rc.get("clk"))}
         del plan, x
     if want("atompar_few_reflections"):
         # many atoms, few reflections: the atom-parallel form (the paper's speed test at 1e6 x 1e3)
@@ -599,13 +629,13 @@ def measure_paths(args, dev, clk, only=None):
         plan = api.Plan(W.unit_species(), W.LATTICE_A, len(rx), s_list=rS, path="generic", timing=True)
         x = torch.tensor(rx, dtype=torch.float64, device=dev)
         out = torch.empty(len(rS), dtype=torch.complex64, device=dev)
-        ms = _time_calls(lambda: plan.amplitude(x, out=out), plan, reps=5)
+        ms = timed(lambda: plan.amplitude(x, out=out), plan, reps=5)
         pairs_a = float(len(rx) * len(rS))
         res["atompar_few_reflections"] = {
             "value": pairs_a / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
             "atoms_per_thread": plan.info()["atoms_per_thread"],
             "workload": "1e6 random atoms x 1000 random reflections (atom-parallel form)",
-            "roofline": _rate_roof(pairs_a, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk, "Gpair/s",
+            "roofline": _rate_roof(pairs_a, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, rc.get("clk"), "Gpair/s",
                                    "alu", "pairs (2 MUFU sin/cos each)")}
         del plan, x, out
     if want("dwba_ge_dot"):
@@ -619,7 +649,7 @@ def measure_paths(args, dev, clk, only=None):
         for name, pth in (("ffma", "generic"), ("separable", "separable")):
             plan = api.Plan(dot.coef, W.LATTICE_A, len(dot.xyz), axes=ax, atom_species=dot.species, gid=gid,
                             path=pth, timing=True)
-            ms = _time_calls(lambda: plan.amplitude(x), plan, reps=2)
+            ms = timed(lambda: plan.amplitude(x), plan, reps=2)
             row[f"{name}_ms"] = ms
             row[f"{name}_value"] = 4 * len(dot.xyz) * m_dot / (ms * 1e-3)
             del plan
@@ -635,14 +665,14 @@ def measure_paths(args, dev, clk, only=None):
                         autotune=True, tune_cache=bcache)
         x = torch.tensor(bx, dtype=torch.float64, device=dev)
         out = torch.empty(len(bS), dtype=torch.complex64, device=dev)
-        ms = _time_calls(lambda: plan.amplitude(x, out=out), plan)
+        ms = timed(lambda: plan.amplitude(x, out=out), plan)
         pairs_b = float(np.sum(np.diff(ao) * np.diff(so)))
         inf = plan.info()
         res["batch_ewald"] = {"value": pairs_b / (ms * 1e-3), "unit": UNIT, "graph_ms": ms, "instances": len(ao) - 1,
                               "tiling": {"threads": inf["threads"], "points_per_thread": inf["points_per_thread"],
                                          "autotuned": True},
                               "workload": f"{len(ao) - 1} fcc crystals 1e3-2e5 atoms, 1e4-1e6 Ewald-slice points each",
-                              "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, clk,
+                              "roofline": _rate_roof(pairs_b, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm, rc.get("clk"),
                                                      "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
     return res
 

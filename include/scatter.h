@@ -67,7 +67,7 @@ typedef enum scatter_s_kind {
 
 /* Kernel family that evaluates the sum. */
 typedef enum scatter_path {
-  SCATTER_PATH_AUTO = 0,      /* the plan picks                                   */
+  SCATTER_PATH_AUTO = 0,      /* the plan picks (scatter_options.tolerance)      */
   SCATTER_PATH_GENERIC = 1,   /* FP32 + MUFU sincos, split phase reduction        */
   SCATTER_PATH_SEPARABLE = 2, /* axis-factorised contraction on tcgen05 (grids)   */
   SCATTER_PATH_FP64_REF = 3   /* plain FP64 kernel: one thread per S, no tricks   */
@@ -165,6 +165,18 @@ typedef struct scatter_options {
                                 the reflections and split the atoms, Section 3)
                                 with that many atoms per thread; 0 = chosen by
                                 the heuristic / autotuner; -1 = never         */
+  double tolerance;          /* SCATTER_PATH_AUTO: the relative L2 error of the
+                                map the caller accepts (0 = 1e-4).  A single
+                                GRID or GID_GRID plan takes the separable
+                                tensor-core path when the grid is large enough
+                                for it and its error model, times a margin
+                                measured against the oracle, stays within the
+                                tolerance; everything else takes the generic
+                                FP32 path                                     */
+  double radius_hint;        /* SCATTER_PATH_AUTO: bound on |r_j - t| (lattice
+                                units, after the integer centring) used by
+                                that error model; 0 = a compact crystal of
+                                n_atoms at 4 atoms per cell                   */
 } scatter_options;
 
 typedef struct scatter_plan_s* scatter_plan_t;

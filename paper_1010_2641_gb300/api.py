@@ -59,13 +59,19 @@ class Plan:
     atoms_per_thread : generic path, one instance: 1/2/4/8/16 forces the
         atom-parallel form (for many atoms and few reflections), 0 lets the
         heuristic or autotuner choose, -1 keeps the S-parallel kernel.
+    path : "auto" (default), "generic", "separable" or "fp64".  With "auto" a
+        grid plan takes the separable tensor-core path when the grid is large
+        enough and its error model (with a measured margin) meets `tolerance`
+        (relative L2 of the map, 0 = 1e-4) for crystals of `radius_hint`
+        lattice units around their centre (0 = compact); otherwise generic.
     """
 
     def __init__(self, coef, lattice_a: float, n_atoms: int, *, s_list=None, axes: Sequence | None = None,
                  atom_species=None, center=None, path: str = "auto", gid: dict | None = None,
                  atom_off=None, s_off=None, autotune: bool = False, tune_cache: str | None = None,
                  threads: int = 0, points_per_thread: int = 0, split_k: int = 0, use_graph: bool = True,
-                 timing: bool = False, atoms_per_thread: int = 0, factor_table=None):
+                 timing: bool = False, atoms_per_thread: int = 0, factor_table=None, tolerance: float = 0.0,
+                 radius_hint: float = 0.0):
         L = B.lib()
         self._keep = []
         pr = B.scatter_problem()
@@ -132,6 +138,8 @@ class Plan:
         op.use_graph = 0 if use_graph else -1
         op.timing = int(bool(timing))
         op.atoms_per_thread = int(atoms_per_thread)
+        op.tolerance = float(tolerance)
+        op.radius_hint = float(radius_hint)
         h = ctypes.c_void_p()
         B.check(L.scatter_plan(ctypes.byref(pr), ctypes.byref(op), ctypes.byref(h)), "scatter_plan")
         self._h = h

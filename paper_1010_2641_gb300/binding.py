@@ -72,7 +72,7 @@ class scatter_problem(ctypes.Structure):
 class scatter_options(ctypes.Structure):
     _fields_ = [("path", c_int32), ("autotune", c_int32), ("tune_cache", c_char_p), ("threads", c_int32),
                 ("points_per_thread", c_int32), ("split_k", c_int32), ("use_graph", c_int32), ("timing", c_int32),
-                ("atoms_per_thread", c_int32)]
+                ("atoms_per_thread", c_int32), ("tolerance", c_double), ("radius_hint", c_double)]
 
 
 class scatter_plan_info(ctypes.Structure):

@@ -220,12 +220,7 @@ extern "C" scatter_status scatter_error_bound(scatter_plan_t p, double radius, d
   const double u = std::ldexp(1.0, -24);  // fp32 unit roundoff
   const double pi = 3.14159265358979323846;
   if (p->path == SCATTER_PATH_SEPARABLE) {
-    // tables in FP32 (sincospif, ~2 ulp) and f16 hi + lo operands (three
-    // products: the dropped lo.lo term is below 2^-22 of each term)
-    const double sr = (p->s_max[0] + p->s_max[1] + p->s_max[2]) * radius;
-    *per_pair = 2.0 * pi * u * (2.0 * sr + 2.0) + 4.0 * std::ldexp(1.0, -22) + 6.0 * u;
-    const double steps = (double)std::max<int64_t>(p->n_slots, 1) / 16.0;
-    *rel_l2_random = *per_pair + u * std::sqrt(4096.0 + steps / 256.0 + (double)p->tiling.split_k);
+    *rel_l2_random = separable_error_model(p, radius, p->tiling.split_k, per_pair);
     return SCATTER_OK;
   }
   if (p->path == SCATTER_PATH_FP64_REF) {

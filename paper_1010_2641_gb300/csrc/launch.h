@@ -56,7 +56,9 @@ scatter_status launch_gid_combine(scatter_plan_t p, float2* amp_out, float* int_
 scatter_status launch_f64_gid(scatter_plan_t p, const double* xyz, const float* occ, float2* amp_out,
                               float* int_out, cudaStream_t st);
 
-// Separable tensor-core path (GRID plans): tables, tiling, launches.
+// Separable tensor-core path (GRID plans): tables, tiling, launches, and its
+// error model (relative L2 of a map with uncorrelated per-term errors).
+double separable_error_model(const scatter_plan_s* p, double radius, int split, double* per_pair);
 scatter_status prepare_separable(scatter_plan_s* p, int split_override);
 scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st);
 

@@ -128,6 +128,50 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
   return SCATTER_OK;
 }
 
+// Error model of the separable path (the relative L2 error of a map whose
+// per-term errors are uncorrelated): tables in FP32 (sincospif, ~2 ulp), f16
+// hi + lo operands with three products (the dropped lo.lo term is below 2^-22
+// of each term), FP32 accumulation in TMEM and in the partials.  `radius`
+// bounds |r - t|; *per_pair receives the per-term bound.
+}  // namespace
+
+double separable_error_model(const scatter_plan_s* p, double radius, int split, double* per_pair) {
+  const double u = std::ldexp(1.0, -24);
+  const double pi = 3.14159265358979323846;
+  const double sr = (p->s_max[0] + p->s_max[1] + p->s_max[2]) * radius;
+  const double pp = 2.0 * pi * u * (2.0 * sr + 2.0) + 4.0 * std::ldexp(1.0, -22) + 6.0 * u;
+  if (per_pair) *per_pair = pp;
+  const double steps = (double)std::max<int64_t>(p->n_slots, 1) / 16.0;
+  return pp + u * std::sqrt(4096.0 + steps / 256.0 + (double)std::max(split, 1));
+}
+
+namespace {
+
+// Measured separable map error over the model above: 3.8e-5 against 1.5e-5
+// on the strained sphere (134,009 atoms, 256 x 256 x 64), i.e. 2.5; AUTO
+// asks the model times this margin to meet the tolerance.
+constexpr double kSepModelMargin = 4.0;
+
+// SCATTER_PATH_AUTO on a single GRID or GID_GRID plan (S tables, instances
+// and slots prepared): the separable tensor-core path when the grid fills its
+// tiles well enough to beat the generic kernel and its error, by the model
+// with the measured margin, stays within the caller's tolerance.
+bool auto_prefers_separable(const scatter_plan_s* p, const scatter_options* op) {
+  if (p->batch != 1 || (p->s_kind != SCATTER_S_GRID && p->s_kind != SCATTER_S_GID_GRID)) return false;
+  if (p->n_slots % 16) return false;
+  const int64_t n0 = p->n_axis[0];
+  const int64_t n12 = p->n_axis[1] * (p->s_kind == SCATTER_S_GID_GRID ? 4 * p->n_axis[2] : p->n_axis[2]);
+  // B rows are formed once per 16 atoms for 2 x 64 values of the first axis:
+  // with fewer than 16 of them, or less than four 256-point column tiles, or
+  // a few hundred steps of atoms, the formation and the fixed costs dominate
+  if (n0 < 16 || n12 < 1024 || p->n_slots < 4096) return false;
+  const double tol = op && op->tolerance > 0.0 ? op->tolerance : 1e-4;
+  const double radius = op && op->radius_hint > 0.0
+                            ? op->radius_hint
+                            : std::cbrt(3.0 * (double)p->n_atoms / (16.0 * 3.14159265358979323846)) + 1.0;
+  return separable_error_model(p, radius, 1, nullptr) * kSepModelMargin <= tol;
+}
+
 // Reference reflection H of one instance: rint of the mean S (or the given
 // center).  S - H is then small, which keeps s . x' small in FP32.
 void choose_H(const scatter_problem* pr, int64_t s_begin, int64_t s_end, double H[3]) {
@@ -314,7 +358,10 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
     if ((e = cudaEventCreate(&p->ev_end)) != cudaSuccess) return cuda_status(e, "cudaEventCreate");
   }
   scatter_path path = op ? (scatter_path)op->path : SCATTER_PATH_AUTO;
-  if (path == SCATTER_PATH_AUTO) path = SCATTER_PATH_GENERIC;
+  // AUTO: generic unless the grid test below (once S and the slots are known)
+  // picks the separable path
+  const bool auto_path = path == SCATTER_PATH_AUTO;
+  if (auto_path) path = SCATTER_PATH_GENERIC;
   if (path == SCATTER_PATH_SEPARABLE && (pr->s_kind == SCATTER_S_LIST || pr->batch != 1))
     return fail(SCATTER_ERR_UNSUPPORTED, "the separable path needs a single axis-aligned grid (GRID or GID_GRID)");
   if (pr->batch > 1 && path != SCATTER_PATH_FP64_REF && path != SCATTER_PATH_GENERIC)
@@ -473,6 +520,10 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   if ((st = upload<double>(&d.loss_part, nullptr, kLossParts, &bytes))) return st;
   p->base_bytes = bytes;
   if (pr->s_kind == SCATTER_S_GID_GRID && (st = prepare_gid(p.get()))) return st;
+  if (auto_path && auto_prefers_separable(p.get(), op)) {
+    path = SCATTER_PATH_SEPARABLE;
+    p->path = path;
+  }
 
   // ---- tiling ------------------------------------------------------------------------
   if (path == SCATTER_PATH_SEPARABLE) {

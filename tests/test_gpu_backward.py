@@ -47,7 +47,7 @@ def _case(radius=3.2, shape=(9, 7, 13), step=0.02, seed=11, occ=False, offset=(0
 @pytest.mark.parametrize("occ,offset", [(False, (0, 0, 0)), (True, (0, 0, 0)), (True, (40.4, -7.7, 13.2))])
 def test_misfit_and_gradient_vs_oracle(occ, offset):
     c, axes, S, I_obs, w = _case(occ=occ, offset=offset)
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="generic")
     xyz = dev(c.xyz, grad=True)
     loss = api.misfit(xyz, plan, dev(I_obs, torch.float32), None if w is None else dev(w, torch.float32))
     loss.backward()
@@ -65,7 +65,7 @@ def test_vjp_through_autograd():
     """Any loss written in torch on A reaches the adjoint kernel through
     ScatterAmplitude.backward (scatter_vjp)."""
     c, axes, S, I_obs, _ = _case(seed=21)
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="generic")
     xyz = dev(c.xyz, grad=True)
     A = api.amplitude(xyz, plan)
     loss = ((A.abs() ** 2 - dev(I_obs, torch.float32)) ** 2).sum()
@@ -98,7 +98,7 @@ def test_strained_cube_all_atoms_subgrid():
     S = W.grid_points(axes)
     pert = W.perturbed_copy(c)
     I_obs = (np.abs(oracle.amplitude(pert.xyz, S, c.coef, A_LAT)) ** 2).astype(np.float32)
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, path="generic")
     x = dev(c.xyz)
     A = plan.amplitude(x)
     loss, grad = plan.backward(x, A, dev(I_obs, torch.float32))
@@ -117,7 +117,7 @@ def test_strained_cube_full_grid_properties():
     c = W.strained_cube()
     axes = [W.linspace_axis(0.0, 128, step=0.005), W.linspace_axis(0.0, 128, step=0.005),
             W.linspace_axis(4.0, 128, step=0.005)]
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, path="generic")
     pert = W.perturbed_copy(c)
     I_obs = plan.intensity(dev(pert.xyz))
     x = dev(c.xyz)
@@ -148,7 +148,7 @@ def test_gradient_line_recurrence_and_fallback(l_axis):
     S = W.grid_points(axes)
     pert = W.perturbed_copy(c, 0.03, seed=22)
     I_obs = (np.abs(oracle.amplitude(pert.xyz, S, c.coef, A_LAT, species=c.species)) ** 2).astype(np.float32)
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="generic")
     x = dev(c.xyz)
     A = plan.amplitude(x)
     loss, grad = plan.backward(x, A, dev(I_obs, torch.float32))

@@ -31,7 +31,7 @@ def small_island():
     return W.truncated_pyramid(base_cells=12, height_cells=5, top_cells=4)
 
 
-def gpu_map(c, axes, path="auto", delta=W.GID_DELTA, beta=W.GID_BETA, occ=None, split_k=0):
+def gpu_map(c, axes, path="generic", delta=W.GID_DELTA, beta=W.GID_BETA, occ=None, split_k=0):
     gid = dict(wavelength=LAM, alpha_i=W.GID_ALPHA_I, delta=delta, beta=beta)
     plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, gid=gid, path=path,
                     split_k=split_k)

@@ -59,7 +59,8 @@ def test_timeout_and_numeric_bits_are_distinct():
 def _small_plan():
     c = W.fcc_sphere(radius_cells=2.5, seed=99)
     axes = [W.linspace_axis(0.0, 9, step=0.01), W.linspace_axis(0.0, 7, step=0.01), W.linspace_axis(4.0, 5, step=0.01)]
-    return c, axes, lambda: api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    return c, axes, lambda: api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species,
+                                     path="generic")
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8])

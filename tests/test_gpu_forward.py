@@ -113,7 +113,7 @@ def test_off_centre_crystal_translation(kind):
         axes = [W.linspace_axis(0.02, 5, step=0.013), W.linspace_axis(-0.01, 7, step=0.011),
                 W.linspace_axis(3.97, 13, step=0.009)]
         S = W.grid_points(axes)
-        plan = api.Plan(coef, A_LAT, len(xyz), axes=axes, atom_species=sp)
+        plan = api.Plan(coef, A_LAT, len(xyz), axes=axes, atom_species=sp, path="generic")
     A = run(plan, xyz, occ)
     assert plan.info()["shift"] == [137.0, -213.0, 55.0]
     ref = oracle.amplitude(xyz, S, coef, A_LAT, species=sp, occ=occ.astype(np.float32))
@@ -126,7 +126,7 @@ def test_grid_ragged(shape):
     axes = [W.linspace_axis(0.0, shape[0], step=0.004), W.linspace_axis(0.0, shape[1], step=0.004),
             W.linspace_axis(4.0, shape[2], step=0.004)]
     S = W.grid_points(axes)
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="generic")
     A = run(plan, c.xyz)
     ref = oracle.amplitude(c.xyz, S, c.coef, A_LAT, species=c.species)
     assert A.shape == (np.prod(shape),)
@@ -215,9 +215,11 @@ def test_autotune_cache(tmp_path):
     c = W.fcc_sphere(radius_cells=5.0, seed=3)
     axes = [W.linspace_axis(0.0, 24, step=0.01), W.linspace_axis(0.0, 24, step=0.01), W.linspace_axis(4.0, 32, step=0.01)]
     cache = tmp_path / "tune.jsonl"
-    p1 = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, autotune=True, tune_cache=str(cache))
+    p1 = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, autotune=True, tune_cache=str(cache),
+                  path="generic")
     assert cache.exists() and cache.read_text().count("\n") == 1
-    p2 = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, autotune=True, tune_cache=str(cache))
+    p2 = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, autotune=True, tune_cache=str(cache),
+                  path="generic")
     assert cache.read_text().count("\n") == 1
     i1, i2 = p1.info(), p2.info()
     assert (i1["threads"], i1["points_per_thread"], i1["split_k"]) == (i2["threads"], i2["points_per_thread"], i2["split_k"])
@@ -248,7 +250,7 @@ def test_strained_sphere_full_size_sampled():
     c = W.fcc_sphere()
     axes = [W.linspace_axis(0.0, 256, step=0.002), W.linspace_axis(0.0, 256, step=0.002),
             W.linspace_axis(4.0, 64, step=0.002)]
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="generic")
     A = run(plan, c.xyz)
     assert A.shape == (256 * 256 * 64,)
     rng = np.random.default_rng(0)

@@ -89,7 +89,7 @@ def test_replayed_map_matches_oracle():
 def test_timing_plans_run_eagerly():
     c = W.fcc_sphere(radius_cells=3.0, seed=93)
     axes = [W.linspace_axis(0.0, 7, step=0.01), W.linspace_axis(0.0, 5, step=0.01), W.linspace_axis(4.0, 9, step=0.01)]
-    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, timing=True)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, timing=True, path="generic")
     x = torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0")
     out = torch.empty(7 * 5 * 9, dtype=torch.complex64, device="cuda:0")
     for _ in range(3):
