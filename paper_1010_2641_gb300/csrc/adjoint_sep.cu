@@ -293,6 +293,7 @@ scatter_status prepare_adjoint_sep(scatter_plan_s* p) {
   if ((e = cudaMalloc(&p->d.adj_gf, gf_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc adjoint gF");
   if ((e = cudaMalloc(&p->d.adj_sexp, sexp_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc row scales");
   if ((e = cudaMalloc(&p->d.adj_sepA, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc adjoint A");
+  if ((e = cudaMemset(p->d.adj_sepA, 0, a_bytes)) != cudaSuccess) return cuda_status(e, "memset adjoint A");
   if ((e = cudaMalloc(&p->d.adj_sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc adjoint partials");
   if ((e = cudaMalloc(&p->d.adj_rec, rec.size() * sizeof(float4))) != cudaSuccess)

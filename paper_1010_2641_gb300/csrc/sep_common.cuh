@@ -110,8 +110,28 @@ struct SepArgs {
   unsigned* status;
 };
 
+// Accumulation groups: the steps between two TMEM flushes (every kSepFlush
+// steps and at the end of the chunk).  Every role walks them identically.
+struct SepGroups {
+  int64_t ks_end, grp_start;
+  __device__ bool ends_at(int64_t ks) const { return ks + 1 == ks_end || ks + 1 - grp_start >= kSepFlush; }
+  __device__ void advance(int64_t ks) { grp_start = ks + 1; }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(dev::smem_addr(bar)) : "memory");
+}
+
 // Launches k_sep on `st` (its shared-memory attribute set by sep_prepare_kernel).
 cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st);
 cudaError_t sep_prepare_kernel();
+// The CTA-pair form (sep_pair.cu): n_nt N tiles, n_chunks atom chunks.
+cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);
+cudaError_t sep_pair_prepare_kernel();
+bool sep_pair_enabled();
+// The CTA-pair form (sep_pair.cu): n_nt N tiles, n_chunks atom chunks.
+cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);
+cudaError_t sep_pair_prepare_kernel();
+bool sep_pair_enabled();
 
 }  // namespace scatter

@@ -109,18 +109,6 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
 // -------------------------------------------------------------------------
 
 
-// Accumulation groups: the steps between two TMEM flushes (every kSepFlush
-// steps and at the end of the chunk).  Both roles walk them identically.
-struct SepGroups {
-  int64_t ks_end, grp_start;
-  __device__ bool ends_at(int64_t ks) const { return ks + 1 == ks_end || ks + 1 - grp_start >= kSepFlush; }
-  __device__ void advance(int64_t ks) { grp_start = ks + 1; }
-};
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(dev::smem_addr(bar)) : "memory");
-}
-
 // Warp roles: warps 0..7 form the B rows (one point per thread) and read the
 // accumulators out at every group end; warp 8 (one lane) issues the MMAs;
 // warp 9 (one lane) issues the TMA copies.  Hand-offs go through mbarriers
@@ -504,10 +492,17 @@ __global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* _
 
 cudaError_t sep_prepare_kernel() {
   static_assert(kSepSmem + 4096 <= 227 * 1024, "dynamic + static shared memory of k_sep");
-  return cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem);
+  const cudaError_t e = cudaFuncSetAttribute(k_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSepSmem);
+  return e != cudaSuccess ? e : sep_pair_prepare_kernel();
 }
 
+// grid: x = M-tile pairs x N tiles, y = chunks.  The CTA-pair kernel
+// (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster.
 cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
+  if (sep_pair_enabled()) {
+    const int64_t n_mp = (a.n_mt + 1) / 2;
+    return sep_pair_launch_core(a, (int64_t)grid.x / n_mp, (int)grid.y, st);
+  }
   k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
   return cudaGetLastError();
 }
@@ -615,6 +610,9 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   const size_t part_bytes = (size_t)p->sep_n_chunks * 2 * (size_t)p->sep_ns * sizeof(float);
   const size_t chunk_bytes = chunks.size() * sizeof(Segment);
   if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
+  // tiles past the last row are never written by the table kernel: zero
+  // them once (the CTA-pair kernel streams the second tile of a pair always)
+  if ((e = cudaMemset(p->d.sep_A, 0, a_bytes)) != cudaSuccess) return cuda_status(e, "memset separable A");
   if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc separable partials");
   if ((e = cudaMalloc(&p->d.sep_chunks, chunk_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc chunks");
