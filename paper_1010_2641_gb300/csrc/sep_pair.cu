@@ -50,7 +50,7 @@ constexpr int kPairHalfN = kSepN / 2;                  // B columns formed per C
 constexpr uint32_t kPairBBytes = 16384;                // B half stage: hi + lo, 128 x 32 f16 each
 constexpr uint32_t kPairTileBytes = kSepABytes;        // one CTA's A tile per step (hi + lo)
 constexpr int kPairAStages = 4;
-constexpr int kPairBStages = 4;
+constexpr int kPairBStages = kPairAStages;  // a step's A and B stages share one "ready" barrier
 constexpr int kPairTStages = 8;
 constexpr size_t kPairSmem = kPairAStages * 2 * kPairTileBytes + kPairBStages * kPairBBytes + 1024;
 // kind::f16, D f32, K-major A and B, N = 256 (>> 3 at bit 17), M = 256 (>> 4 at bit 24)
@@ -122,22 +122,21 @@ __device__ __forceinline__ void commit_pair(uint64_t* bar) {
 
 // Barriers (every CTA holds the full set; the ones marked "rank 0" only carry
 // arrivals in rank 0):
-//   bar_full[a]   this CTA's A blocks of a step arrived        (TMA)
-//   bar_done[a]   the pair's MMAs of the step completed         (multicast commit)
+//   bar_ready[s]  stage s of a step is ready: this CTA's A blocks arrived
+//                 (TMA: the copy warp's arrival + bytes), its B half formed
+//                 (8 warps) and, in rank 0, rank 1's stage ready (relay):
+//                 the MMA thread's only wait per step
+//   bar_done[s]   the pair's MMAs of the step completed         (multicast commit)
 //   bar_atom[t]   atom records of a step arrived                (TMA)
 //   bar_tempty[t] atom records read by this CTA's formation     (8 warps)
-//   bar_bformed[b] this CTA's B half of a step formed           (8 warps)
-//   bar_peer[b]   rank 0: rank 1's A and B of the step are ready (relay)
 //   bar_tread     this CTA's accumulators read out              (8 warps)
 //   bar_pfree     rank 0: rank 1's accumulators read out        (relay)
 __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepArgs a) {
   extern __shared__ __align__(1024) unsigned char pair_smem_raw[];
-  __shared__ __align__(8) uint64_t bar_full[kPairAStages];
+  __shared__ __align__(8) uint64_t bar_ready[kPairAStages];
   __shared__ __align__(8) uint64_t bar_done[kPairAStages];
   __shared__ __align__(8) uint64_t bar_atom[kPairTStages];
   __shared__ __align__(8) uint64_t bar_tempty[kPairTStages];
-  __shared__ __align__(8) uint64_t bar_bformed[kPairBStages];
-  __shared__ __align__(8) uint64_t bar_peer[kPairBStages];
   __shared__ __align__(8) uint64_t bar_tread;
   __shared__ __align__(8) uint64_t bar_pfree;
   __shared__ __align__(16) float4 ring_atom[kPairTStages][kSepStep];
@@ -175,16 +174,12 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   }
   if (tid == 0) {
     for (int s = 0; s < kPairAStages; ++s) {
-      dev::mbar_init(&bar_full[s], 1);
+      dev::mbar_init(&bar_ready[s], 1 + kSepFormWarps + (rank == 0 ? 1 : 0));
       dev::mbar_init(&bar_done[s], 1);
     }
     for (int s = 0; s < kPairTStages; ++s) {
       dev::mbar_init(&bar_atom[s], 1);
       dev::mbar_init(&bar_tempty[s], kSepFormWarps);
-    }
-    for (int s = 0; s < kPairBStages; ++s) {
-      dev::mbar_init(&bar_bformed[s], kSepFormWarps);
-      dev::mbar_init(&bar_peer[s], 1);
     }
     dev::mbar_init(&bar_tread, kSepFormWarps);
     dev::mbar_init(&bar_pfree, 1);
@@ -228,11 +223,11 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
           ok = false;
           break;
         }
-        dev::mbar_arrive_expect_tx(&bar_full[ast], (uint32_t)ntp * kPairTileBytes);
+        dev::mbar_arrive_expect_tx(&bar_ready[ast], (uint32_t)ntp * kPairTileBytes);
         for (int tp = 0; tp < ntp; ++tp)
           dev::bulk_g2s(ringA + (ast * 2 + tp) * kPairTileBytes,
                         Abase + (2 * mq + tp) * pair_stride + ks * (kSepPair * kSepABytes / 16), kPairTileBytes,
-                        &bar_full[ast]);
+                        &bar_ready[ast]);
         a_issued = g + 1;
       }
     }
@@ -258,10 +253,8 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
           ok = false;
           break;
         }
-        const int ast = (int)(g % kPairAStages), bst = (int)(g % kPairBStages);
-        const uint32_t bpar = (uint32_t)((g / kPairBStages) & 1);
-        if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g / kPairAStages) & 1)) ||
-            !dev::mbar_wait_bounded(&bar_bformed[bst], bpar) || !wait_cluster_bounded(&bar_peer[bst], bpar)) {
+        const int ast = (int)(g % kPairAStages), bst = ast;
+        if (!wait_cluster_bounded(&bar_ready[ast], (uint32_t)((g / kPairAStages) & 1))) {
           ok = false;
           break;
         }
@@ -294,13 +287,12 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
           ok = false;
           break;
         }
-        const int ast = (int)(g % kPairAStages), bst = (int)(g % kPairBStages);
-        if (!dev::mbar_wait_bounded(&bar_full[ast], (uint32_t)((g / kPairAStages) & 1)) ||
-            !dev::mbar_wait_bounded(&bar_bformed[bst], (uint32_t)((g / kPairBStages) & 1))) {
+        const int ast = (int)(g % kPairAStages);
+        if (!dev::mbar_wait_bounded(&bar_ready[ast], (uint32_t)((g / kPairAStages) & 1))) {
           ok = false;
           break;
         }
-        arrive_at(&bar_peer[bst], 0);
+        arrive_at(&bar_ready[ast], 0);
         if (grp.ends_at(ks)) {
           if (!dev::mbar_wait_bounded(&bar_tread, (uint32_t)(flushes & 1))) {
             ok = false;
@@ -401,7 +393,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&bar_bformed[bst]);
+        mbar_arrive(&bar_ready[bst]);
         mbar_arrive(&bar_tempty[tst]);
       }
       if (!grp.ends_at(ks)) continue;
@@ -488,7 +480,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   }
   if (copy_warp && lane == 0 && s_abort) {
     for (int64_t s = a_issued > kPairAStages ? a_issued - kPairAStages : 0; s < a_issued; ++s)
-      dev::mbar_wait_bounded(&bar_full[s % kPairAStages], (uint32_t)((s / kPairAStages) & 1), 1LL << 28);
+      dev::mbar_wait_bounded(&bar_ready[s % kPairAStages], (uint32_t)((s / kPairAStages) & 1), 1LL << 28);
     for (int64_t s = t_issued > kPairTStages ? t_issued - kPairTStages : 0; s < t_issued; ++s)
       dev::mbar_wait_bounded(&bar_atom[s % kPairTStages], (uint32_t)((s / kPairTStages) & 1), 1LL << 28);
   }
