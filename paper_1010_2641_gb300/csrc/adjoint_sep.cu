@@ -124,7 +124,8 @@ __global__ void k_adj_sep_tab(const AdjSepTabArgs t) {
 }
 
 struct AdjSepFinalArgs {
-  const float* partial;    // [chunk][Re, Im][3 n0][n_slots]
+  const float* partial;    // [chunk] blocked as sep_part_off: rows 2 (w n0 + a) + {Re, Im}, columns slots
+  int64_t chunk_floats, n_cb;
   int n_chunks;
   const Segment* ntiles;
   const int* sexp;
@@ -175,8 +176,9 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
         if (a < f.n0) {
           const int64_t row = w * f.n0 + a;
           for (int c = 0; c < f.n_chunks; ++c) {
-            U[u][w][0] += f.partial[((int64_t)(2 * c) * rows + row) * f.n_slots + slot];
-            U[u][w][1] += f.partial[((int64_t)(2 * c + 1) * rows + row) * f.n_slots + slot];
+            const float* pc = f.partial + (int64_t)c * f.chunk_floats;
+            U[u][w][0] += pc[sep_part_off(2 * row, slot, f.n_cb)];
+            U[u][w][1] += pc[sep_part_off(2 * row + 1, slot, f.n_cb)];
           }
         }
       }
@@ -268,7 +270,7 @@ scatter_status prepare_adjoint_sep(scatter_plan_s* p) {
   }
   if (ntiles.empty()) return SCATTER_OK;  // no atoms: the FP32 path writes the empty gradient
   const size_t a_bytes = (size_t)p->n_species * (size_t)n_mp * (size_t)n_ksteps * kSepPair * kSepABytes;
-  const size_t part1 = (size_t)2 * 3 * (size_t)n0 * (size_t)p->n_slots * sizeof(float);
+  const size_t part1 = (size_t)sep_part_floats(n_mt, p->n_slots) * sizeof(float);
   const int split = adj_sep_split(p, n_mp * (int64_t)ntiles.size(), n_ksteps, part1);
   std::vector<Segment> chunks;
   const int64_t per = (n_ksteps + split - 1) / split;
@@ -357,9 +359,8 @@ scatter_status launch_adjoint_sep(scatter_plan_t p, float* grad, cudaStream_t st
   a.n0 = n0;
   a.n1 = n1;
   a.n2 = n2;
-  a.n_rows = 3 * n0;
-  a.ld = p->n_slots;
-  a.plane = 3 * n0 * p->n_slots;
+  a.n_cb = (p->n_slots + 31) / 32;
+  a.chunk_floats = sep_part_floats(p->adj_sep_mt, p->n_slots);
   a.n_steps = p->adj_sep_ksteps;
   a.n_mt = p->adj_sep_mt;
   a.partial = p->d.adj_sep_partial;
@@ -371,6 +372,8 @@ scatter_status launch_adjoint_sep(scatter_plan_t p, float* grad, cudaStream_t st
   if (le != cudaSuccess) return cuda_status(le, "adjoint contraction launch");
   AdjSepFinalArgs f{};
   f.partial = p->d.adj_sep_partial;
+  f.chunk_floats = sep_part_floats(p->adj_sep_mt, p->n_slots);
+  f.n_cb = (p->n_slots + 31) / 32;
   f.n_chunks = p->adj_sep_chunks;
   f.ntiles = p->d.adj_ntiles;
   f.sexp = p->d.adj_sexp;

@@ -102,13 +102,28 @@ struct SepArgs {
   const double* shift;             // instance 0: its centring t
   float smax_b, smax_c;            // max |s| of the b and c axes
   int64_t n0, n1, n2;     // grid shape
-  int64_t n_rows;         // rows of each partial plane (forward n0, adjoint 3 n0)
-  int64_t ld;             // floats between rows of a plane (forward n1 n2, adjoint n_slots)
-  int64_t plane;          // floats per plane
   int64_t n_steps, n_mt;  // K steps per A table, M tiles
-  float* partial;         // [chunk][Re, Im][n_rows][ld] planar, raw D (no f_s)
+  int64_t n_cb;           // 32-column blocks of the partials (ceil(columns / 32))
+  int64_t chunk_floats;   // floats of one chunk's partials (sep_part_floats)
+  float* partial;         // [chunk] blocked as sep_part_off, raw D (no f_s)
   unsigned* status;
 };
+
+// Partials in the accumulator's own blocking.  D row m (TMEM lane of its M
+// tile: m = 2 pa + ri, Re or Im of row pa) and column c live at
+//   (((m / 32) n_cb + c / 32) 8 + (c % 32) / 4) 128 + (m % 32) 4 + c % 4
+// floats into a chunk's partials: the 32 x 32 block a warp reads from TMEM
+// with one 32x32b.x32 load is 4 KB contiguous, and each of the warp's eight
+// float4 stores or reductions covers 512 contiguous bytes (lane l holds row
+// m0 + l, columns 4 q .. 4 q + 3 at float4 q * 32 + l of the block).
+__host__ __device__ __forceinline__ int64_t sep_part_off(int64_t m, int64_t c, int64_t n_cb) {
+  return ((((m >> 5) * n_cb + (c >> 5)) * 8 + ((c & 31) >> 2)) << 7) + ((m & 31) << 2) + (c & 3);
+}
+// floats per chunk: every row of n_mt M tiles rounded up to pairs, columns
+// rounded up to blocks of 32
+inline int64_t sep_part_floats(int64_t n_mt, int64_t n_cols) {
+  return ((n_mt + 1) / 2) * 2 * 128 * ((n_cols + 31) / 32) * 32;
+}
 
 // Accumulation groups: the steps between two TMEM flushes (every kSepFlush
 // steps and at the end of the chunk).  Every role walks them identically.

@@ -341,8 +341,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         exact = bound > dev::kPhaseExactLim;
       }
     }
-    float* part_re = a.partial + (int64_t)chunk * 2 * a.plane;
-    float* part_im = part_re + a.plane;
+    float* part = a.partial + (int64_t)chunk * a.chunk_floats;
     bool first_flush = true;
     int64_t g = 0;
     for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -398,49 +397,37 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       }
       if (!grp.ends_at(ks)) continue;
 
-      // ---- group end: this CTA's TMEM -> planar partials -----------------------
+      // ---- group end: this CTA's TMEM -> blocked partials ----------------------
       w = dev::mbar_wait_bounded(&bar_done[g % kPairAStages], (uint32_t)((g / kPairAStages) & 1));
       if (!__all_sync(0xffffffffu, w)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      // TMEM lane = this CTA's row 2 pa + ri of tile 2 p + rank
+      // TMEM lane = row (2 pa + ri) of this CTA's tile: one 32 x 32 block of
+      // the partials per load; padding rows and columns are written too
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m_row = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32 + lane;
-        const int64_t pa = m_row >> 1;
-        float* plane = (m_row & 1) ? part_im : part_re;
+        const int64_t m0 = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
           const int64_t bc0 = col_base + col0 + cc;
-          float* dst = plane + pa * a.ld + bc0;
-          const bool row_in = pa < a.n_rows && bc0 < col_end;
-          const bool vec = row_in && bc0 + 32 <= col_end && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+          if (bc0 >= col_end) break;
+          float4* blk = reinterpret_cast<float4*>(part + sep_part_off(m0, bc0, a.n_cb)) + lane;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
-          // first read-out stores, later ones add in L2 (one owner per
-          // element, program order: deterministic sums)
-          if (vec) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
+          // the first read-out stores, later ones add in L2 (reductions, no
+          // load round trip); every element belongs to this CTA and its
+          // updates come from this thread in program order, so the sum is
+          // deterministic
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-              if (first_flush)
-                d4[q] = x;
-              else
-                atomicAdd(d4 + q, x);
-            }
-          } else if (row_in) {
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-              if (bc0 + q < col_end) {
-                if (first_flush)
-                  dst[q] = v[q];
-                else
-                  atomicAdd(dst + q, v[q]);
-              }
+          for (int q = 0; q < 8; ++q) {
+            const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            if (first_flush)
+              blk[q * 32] = x;
+            else
+              atomicAdd(blk + q * 32, x);
           }
         }
       }
@@ -455,11 +442,10 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m_row = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32 + lane;
-        const int64_t pa = m_row >> 1;
-        if (pa < a.n_rows) {
-          float* dst = ((m_row & 1) ? part_im : part_re) + pa * a.ld + col_base + col0;
-          for (int q = 0; q < 128 && col_base + col0 + q < col_end; ++q) dst[q] = 0.f;
+        const int64_t m0 = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32;
+        for (int cc = 0; cc < 128 && col_base + col0 + cc < col_end; cc += 32) {
+          float4* blk = reinterpret_cast<float4*>(part + sep_part_off(m0, col_base + col0 + cc, a.n_cb)) + lane;
+          for (int q = 0; q < 8; ++q) blk[q * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     }

@@ -35,7 +35,8 @@
 // and the B stores.
 // Atom chunks (grid y) hold one species each.  Every 256 steps and at the
 // end of the chunk the accumulator is read from TMEM (tcgen05.ld) and added
-// into planar FP32 partials owned by the CTA (shorter groups keep the
+// into FP32 partials owned by the CTA, in the accumulator's 32 x 32 blocks
+// (sep_part_off; shorter groups keep the
 // tensor core's FP32 accumulation error down); k_sep_reduce sums the chunks
 // in order, each times its species' f_s(|S|), and applies the translation
 // phase.
@@ -307,8 +308,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         exact = bound > dev::kPhaseExactLim;
       }
     }
-    float* part_re = a.partial + (int64_t)chunk * 2 * a.plane;
-    float* part_im = part_re + a.plane;
+    float* part = a.partial + (int64_t)chunk * a.chunk_floats;
     bool first_flush = true;
     int64_t g = 0;
     for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
@@ -365,7 +365,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       }
       if (!grp.ends_at(ks)) continue;
 
-      // ---- group end: TMEM -> planar partials --------------------------------
+      // ---- group end: TMEM -> blocked partials -------------------------------
       // the commit of step g covers every earlier MMA of the group
       w = dev::mbar_wait_bounded(&bar_done[g % kSepAStages], (uint32_t)((g / kSepAStages) & 1));
       if (!__all_sync(0xffffffffu, w)) {
@@ -373,45 +373,30 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
         break;
       }
       tc_fence_after();
-      // TMEM lane = A row 2 pa + ri: this thread's row is Re D (ri = 0) or
-      // Im D (ri = 1) of row pa, i.e. one plane of the partials
+      // TMEM lane = row (2 pa + ri) of this CTA's tile: one 32 x 32 block of
+      // the partials per load; padding rows and columns are written too
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
-        const int64_t pa = m_row >> 1;
-        float* plane = (m_row & 1) ? part_im : part_re;
+        const int64_t m0 = (2 * mp + tp) * kSepM + sub * 32;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
           const int64_t bc0 = col_base + col0 + cc;
-          float* dst = plane + pa * a.ld + bc0;
-          const bool row_in = pa < a.n_rows && bc0 < col_end;
-          const bool vec = row_in && bc0 + 32 <= col_end && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+          if (bc0 >= col_end) break;
+          float4* blk = reinterpret_cast<float4*>(part + sep_part_off(m0, bc0, a.n_cb)) + lane;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(tp * kSepN + col0 + cc), v);
           // the first read-out stores, later ones add in L2 (reductions, no
           // load round trip); every element belongs to this CTA and its
           // updates come from this thread in program order, so the sum is
           // deterministic
-          if (vec) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-              if (first_flush)
-                d4[q] = x;
-              else
-                atomicAdd(d4 + q, x);
-            }
-          } else if (row_in) {
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-              if (bc0 + q < col_end) {
-                if (first_flush)
-                  dst[q] = v[q];
-                else
-                  atomicAdd(dst + q, v[q]);
-              }
+          for (int q = 0; q < 8; ++q) {
+            const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            if (first_flush)
+              blk[q * 32] = x;
+            else
+              atomicAdd(blk + q * 32, x);
           }
         }
       }
@@ -426,11 +411,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m_row = (2 * mp + tp) * kSepM + sub * 32 + lane;
-        const int64_t pa = m_row >> 1;
-        if (pa < a.n_rows) {
-          float* dst = ((m_row & 1) ? part_im : part_re) + pa * a.ld + col_base + col0;
-          for (int q = 0; q < 128 && col_base + col0 + q < col_end; ++q) dst[q] = 0.f;
+        const int64_t m0 = (2 * mp + tp) * kSepM + sub * 32;
+        for (int cc = 0; cc < 128 && col_base + col0 + cc < col_end; cc += 32) {
+          float4* blk = reinterpret_cast<float4*>(part + sep_part_off(m0, col_base + col0 + cc, a.n_cb)) + lane;
+          for (int q = 0; q < 8; ++q) blk[q * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     }
@@ -459,7 +443,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 
 // Sum over the chunks in order of f_s(|S|) x T_chunk (Eq. 2: each chunk holds
 // one species s), translation phase, outputs.
-__global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* __restrict__ chunks, int n_chunks,
+__global__ void k_sep_reduce(const float* __restrict__ partial, int64_t chunk_floats, int64_t n_cb,
+                             const Segment* __restrict__ chunks, int n_chunks,
                              const float* __restrict__ coef, const float2* __restrict__ ftab, float inv4a2, int64_t n_s,
                              const double* __restrict__ axis64, int64_t n0, int64_t n1, int64_t n2, double H0,
                              double H1, double H2, const double* __restrict__ shift, float2* out_amp, float* out_int) {
@@ -476,7 +461,9 @@ __global__ void k_sep_reduce(const float* __restrict__ partial, const Segment* _
       F = ftab ? ftab[(int64_t)sp * n_s + m] : dev::form_factor(coef + kNCoef * sp, s2);
       cur = sp;
     }
-    const float re = partial[(int64_t)c * 2 * n_s + m], im = partial[(int64_t)c * 2 * n_s + n_s + m];
+    const float* pc = partial + (int64_t)c * chunk_floats;
+    const int64_t col = m - i0 * n1 * n2;  // the point's (b, c) column
+    const float re = pc[sep_part_off(2 * i0, col, n_cb)], im = pc[sep_part_off(2 * i0 + 1, col, n_cb)];
     v.x += F.x * re - F.y * im;
     v.y += F.x * im + F.y * re;
   }
@@ -497,12 +484,13 @@ cudaError_t sep_prepare_kernel() {
 }
 
 // grid: x = M-tile pairs x N tiles, y = chunks.  The CTA-pair kernel
-// (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster.
+// (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster; with
+// an odd number of pairs one cluster per N tile would run one accumulator
+// tile against a full B formation, so those grids keep the one-CTA kernel.
 cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
-  if (sep_pair_enabled()) {
-    const int64_t n_mp = (a.n_mt + 1) / 2;
+  const int64_t n_mp = (a.n_mt + 1) / 2;
+  if (sep_pair_enabled() && n_mp % 2 == 0)
     return sep_pair_launch_core(a, (int64_t)grid.x / n_mp, (int)grid.y, st);
-  }
   k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
   return cudaGetLastError();
 }
@@ -516,7 +504,7 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
   int best_k = 1;
   for (int k = 1; k <= 64; ++k) {
     if (k > 1 && steps / k < 64) break;
-    // one step ~1 us of MMA; an extra chunk costs one planar partial of the
+    // one step ~1 us of MMA; an extra chunk costs one partial of the
     // map (8 B per point written once, read once by the reduction)
     const double part_steps = 16.0 * (double)p->sep_ns / 6.0e12 / 1.0e-6;
     const double cost = std::ceil((double)tiles * k / cap) * (steps / k + 40.0) + (k > 1 ? k * part_steps : 0.0);
@@ -579,7 +567,7 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   t.threads = 256;
   t.R = 8;
   t.split_k = split;
-  // chunk tables (segments) as for the generic path; the partial buffer is planar
+  // chunk tables (segments) as for the generic path; the partial buffer is blocked
   scatter_status st = apply_tiling(p, t);
   if (st != SCATTER_OK) return st;
   if (p->d.partial) {  // the generic path's partials are not used here
@@ -607,7 +595,8 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   }
   if (chunks.empty()) chunks.push_back(Segment{0, 0, 0, 0});  // no atoms: one empty chunk, zero partials
   p->sep_n_chunks = (int32_t)chunks.size();
-  const size_t part_bytes = (size_t)p->sep_n_chunks * 2 * (size_t)p->sep_ns * sizeof(float);
+  const size_t part_bytes =
+      (size_t)p->sep_n_chunks * (size_t)sep_part_floats(n_mt, p->sep_n[1] * p->sep_n[2]) * sizeof(float);
   const size_t chunk_bytes = chunks.size() * sizeof(Segment);
   if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
   // tiles past the last row are never written by the table kernel: zero
@@ -668,9 +657,8 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.n0 = p->sep_n[0];
   a.n1 = p->sep_n[1];
   a.n2 = p->sep_n[2];
-  a.n_rows = p->sep_n[0];
-  a.ld = p->sep_n[1] * p->sep_n[2];
-  a.plane = p->sep_ns;
+  a.n_cb = (p->sep_n[1] * p->sep_n[2] + 31) / 32;
+  a.chunk_floats = sep_part_floats(p->sep_mt, p->sep_n[1] * p->sep_n[2]);
   a.n_steps = p->sep_steps;
   a.n_mt = p->sep_mt;
   a.partial = p->d.sep_partial;
@@ -683,7 +671,8 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
-      p->d.sep_partial, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
+      p->d.sep_partial, sep_part_floats(p->sep_mt, p->sep_n[1] * p->sep_n[2]),
+      (p->sep_n[1] * p->sep_n[2] + 31) / 32, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
       (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
       p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
       p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, gid ? p->d.sep_virt : amp_out,
