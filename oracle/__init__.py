@@ -16,6 +16,7 @@ Every function below follows the paper's definitions:
                reading, the paper prints none)
   loss_grad    L = sum (|A|^2 - I_obs)^2 and its analytic gradient
   fd_grad      central finite differences of L (a second route to the gradient)
+  loss_grad_table  L and the analytic gradient of Eq. 4 (block origins, F fixed)
   loss_grad_atoms  L and the analytic gradient of selected atoms from a map
                the caller already has (large maps summed once)
 """
@@ -65,6 +66,7 @@ def _load():
         lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
         lib.oracle_fd_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, i64, P, f64, P]
+        lib.oracle_loss_grad_table.argtypes = [i64, P, P, P, i32, P, i64, P, P, P, P]
         lib.oracle_loss_grad_given_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, i64, P, P, P]
         lib.oracle_fd_grad_given_amplitude.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, i64, P, f64, P]
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -207,6 +209,24 @@ def fd_grad(xyz, S, I_obs, coef, lattice_a, atoms, h=1e-5, species=None, occ=Non
                                                _ptr(coef), float(lattice_a), S.shape[0], _ptr(S), _ptr(A2),
                                                _ptr(I_obs), sel.shape[0], _ptr(sel), float(h), _ptr(out))
     return out
+
+
+def loss_grad_table(xyz, S, I_obs, table, types=None, occ=None, grad=True):
+    """(L, dL/dr [N,3] or None) of Eq. 4: blocks with the complex factor
+    table F [n_types, M] held fixed, positions the block origins."""
+    xyz = _f64(xyz, 3)
+    n = xyz.shape[0]
+    t = None if types is None else np.ascontiguousarray(np.asarray(types, dtype=np.int32).reshape(n))
+    w = None if occ is None else _f64(occ).reshape(n)
+    S = _f64(S, 3)
+    I_obs = _f64(I_obs).reshape(S.shape[0])
+    tab = np.asarray(table, dtype=np.complex128).reshape(-1, S.shape[0])
+    tab2 = np.ascontiguousarray(np.stack([tab.real, tab.imag], -1))
+    loss = ctypes.c_double()
+    g = np.zeros((n, 3)) if grad else None
+    _load().oracle_loss_grad_table(n, _ptr(xyz), _ptr(t), _ptr(w), tab.shape[0], _ptr(tab2), S.shape[0], _ptr(S),
+                                   _ptr(I_obs), ctypes.byref(loss), _ptr(g))
+    return loss.value, g
 
 
 def loss_grad_atoms(xyz, S, A, I_obs, coef, lattice_a, atoms, species=None, occ=None):

@@ -308,6 +308,50 @@ void oracle_loss_grad(int64_t n_atoms, const double* xyz, const int32_t* species
 }
 
 /*
+ * Misfit and analytic gradient of Eq. 4 (blocks with per-(type, S) factors
+ * F_t(S) from a table [n_types][n_s][2], block origins r_j = r_j^0 + u_j),
+ * F held fixed:
+ *   dL/dr_j = -2 pi sum_S S * Im( g(S) w_j F_{t(j)}(S) exp(2 i pi S.r_j) ),
+ *   g(S) = 4 (|A(S)|^2 - I_obs(S)) conj(A(S)),  A from oracle_amplitude_table.
+ * grad out [n_atoms][3] (may be NULL), *loss out.
+ */
+void oracle_loss_grad_table(int64_t n_atoms, const double* xyz, const int32_t* types,
+                            const double* occ, int32_t n_types, const double* table,
+                            int64_t n_s, const double* S, const double* I_obs,
+                            double* loss, double* grad) {
+  double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
+  double* g = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
+  oracle_amplitude_table(n_atoms, xyz, types, occ, n_types, table, n_s, S, A);
+  *loss = misfit_and_g(n_s, A, I_obs, g);
+  if (grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < n_atoms; ++j) {
+      const double* r = xyz + 3 * j;
+      const double w = occ ? occ[j] : 1.0;
+      const int32_t t = types ? types[j] : 0;
+      double gx = 0.0, gy = 0.0, gz = 0.0;
+      for (int64_t m = 0; m < n_s; ++m) {
+        const double* Sm = S + 3 * m;
+        const double fr = table[2 * (t * n_s + m)], fi = table[2 * (t * n_s + m) + 1];
+        const double phase = 2.0 * kPi * (Sm[0] * r[0] + Sm[1] * r[1] + Sm[2] * r[2]);
+        const double c = cos(phase), s = sin(phase);
+        /* e = w F (c + i s);  Im(g e) */
+        const double er = w * (fr * c - fi * s), ei = w * (fr * s + fi * c);
+        const double im_ge = g[2 * m] * ei + g[2 * m + 1] * er;
+        gx += Sm[0] * im_ge;
+        gy += Sm[1] * im_ge;
+        gz += Sm[2] * im_ge;
+      }
+      grad[3 * j] = -2.0 * kPi * gx;
+      grad[3 * j + 1] = -2.0 * kPi * gy;
+      grad[3 * j + 2] = -2.0 * kPi * gz;
+    }
+  }
+  free(A);
+  free(g);
+}
+
+/*
  * The same misfit and analytic gradient, for the selected atoms only and from
  * an amplitude map A [n_s][2] the caller already has (oracle_amplitude's
  * output): for maps too large to sum more than once.

@@ -411,6 +411,48 @@ def test_blocks_of_fcc_cells_equal_the_atom_sum():
     assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
 
 
+def test_block_gradient_is_the_sum_of_its_atoms_gradients():
+    """A rigid block moves all its atoms together, so dL/d(origin) of Eq. 4
+    (F_t = sum_a f e^{2 i pi S.rho_a} held fixed) equals the sum of Eq. 2's
+    dL/dr over the block's atoms: two independent routes to the gradient."""
+    rng = np.random.default_rng(43)
+    cells = np.stack(np.meshgrid(np.arange(3), np.arange(3), np.arange(2), indexing="ij"), -1).reshape(-1, 3)
+    R = cells + rng.normal(0, 0.04, cells.shape)
+    btype = (rng.uniform(size=len(R)) < 0.4).astype(np.int32)
+    rho = _fcc_block()
+    S = rng.uniform(-0.4, 0.4, (60, 3)) + np.array([1.0, 1.0, 3.0])
+    coef = W.si_ge_species()
+    q = np.linalg.norm(S, axis=1) / W.LATTICE_A
+    f = np.array([[oracle.form_factor(coef[t], qq) for qq in q] for t in range(2)])
+    table = f * np.exp(2j * np.pi * (S @ rho.T)).sum(1)[None, :]
+    atoms = (R[:, None, :] + rho[None, :, :]).reshape(-1, 3)
+    species = np.repeat(btype, len(rho))
+    I_obs = rng.uniform(0, 1, len(S)) * np.abs(oracle.amplitude(atoms, S, coef, W.LATTICE_A, species=species)) ** 2
+    L_blk, g_blk = oracle.loss_grad_table(R, S, I_obs, table, types=btype)
+    L_at, g_at = oracle.loss_grad(atoms, S, I_obs, coef, W.LATTICE_A, species=species)
+    assert abs(L_blk - L_at) < 1e-10 * L_at
+    g_sum = g_at.reshape(len(R), len(rho), 3).sum(1)
+    assert np.allclose(g_blk, g_sum, rtol=1e-9, atol=1e-9 * np.abs(g_sum).max())
+
+
+def test_table_gradient_of_form_factors_is_eq2_gradient():
+    """Single-atom blocks with F_t(S) = f_t(|S|) and occupancies: the Eq. 4
+    gradient is Eq. 2's."""
+    rng = np.random.default_rng(44)
+    xyz = rng.uniform(-5, 5, (40, 3))
+    types = (rng.uniform(size=40) < 0.5).astype(np.int32)
+    occ = rng.uniform(0.3, 1.0, 40)
+    S = rng.uniform(-2, 2, (25, 3)) + np.array([0, 0, 4.0])
+    coef = W.si_ge_species()
+    q = np.linalg.norm(S, axis=1) / W.LATTICE_A
+    table = np.array([[oracle.form_factor(coef[t], qq) for qq in q] for t in range(2)])
+    I_obs = rng.uniform(0, 50, len(S))
+    L1, g1 = oracle.loss_grad_table(xyz, S, I_obs, table, types=types, occ=occ)
+    L2, g2 = oracle.loss_grad(xyz, S, I_obs, coef, W.LATTICE_A, species=types, occ=occ)
+    assert abs(L1 - L2) < 1e-11 * L2
+    assert np.allclose(g1, g2, rtol=1e-10, atol=1e-10 * np.abs(g2).max())
+
+
 def test_table_occupancy_and_duplication():
     rng = np.random.default_rng(42)
     xyz = rng.uniform(-4, 4, (20, 3))
