@@ -138,9 +138,12 @@ typedef struct scatter_problem {
    * M the output points in output order.  When set, the "species" are
    * block types and F_t(S_m) = factor_table[t][m] replaces the Gaussian
    * form factor (the species coefficients are then unused); positions are
-   * the displaced block origins.  LIST and GRID plans of one instance,
-   * forward only (scatter_backward/scatter_vjp return UNSUPPORTED).
-   * Copied at plan time.  NULL: the form factors of `species`.            */
+   * the displaced block origins.  LIST plans (one instance or a batch:
+   * M counts the points of every instance) and GRID plans; the backward
+   * and vjp give dL/d(block origin) with F held fixed.  GID_GRID plans
+   * reject a table (their four beams each have their own S, so one factor
+   * per point does not define the sum).  Copied at plan time.  NULL: the
+   * form factors of `species`.                                            */
   const double* factor_table;
 } scatter_problem;
 

@@ -46,6 +46,7 @@ struct LossArgs {
   double H[3];
   const double* shift;
   const float* coef;
+  const float2* ftab;     // Eq. 4 factor table [n_species][M] (F_t(S) of block types), or null
   int n_species;
   float inv4a2;
   int layout;             // 0: rows {s, gF.re | S, gF.im} for k_adjoint; 1: compact rows
@@ -90,7 +91,8 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a)
     const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
     const float sx = (float)(S[0] - a.H[0]), sy = (float)(S[1] - a.H[1]), sz = (float)(S[2] - a.H[2]);
     for (int sp = 0; sp < a.n_species; ++sp) {
-      const float2 gF = dev::cmul(gp, dev::form_factor(a.coef + kNCoef * sp, s2));
+      const float2 F = a.ftab ? a.ftab[(int64_t)sp * a.n_s + m] : dev::form_factor(a.coef + kNCoef * sp, s2);
+      const float2 gF = dev::cmul(gp, F);
       if (a.layout == 2) {
         a.gf[(int64_t)sp * a.n_s + m] = gF;
       } else if (a.layout == 1) {
@@ -496,7 +498,6 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
                                cudaStream_t st) {
   if (p->path == SCATTER_PATH_FP64_REF)
     return fail(SCATTER_ERR_UNSUPPORTED, "backward runs on the generic path; plan with SCATTER_PATH_GENERIC");
-  if (p->d.ftab) return fail(SCATTER_ERR_UNSUPPORTED, "backward with a factor table (Eq. 4 blocks) is not available");
   scatter_status s = SCATTER_OK;
   if (grad) {
     if ((s = prepare_adjoint(p)) != SCATTER_OK) return s;
@@ -524,6 +525,7 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
   for (int d = 0; d < 3; ++d) la.H[d] = p->inst[0].H[d];
   la.shift = p->d.inst_shift;
   la.coef = p->d.coef;
+  la.ftab = p->d.ftab;  // Eq. 4: the block factors F_t(S) in place of f_s(|S|), held fixed
   la.n_species = grad ? p->n_species : 0;
   la.inv4a2 = (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a));
   la.layout = !grad ? 0 : (p->adj_sep ? 2 : (p->adj_line ? 1 : 0));

@@ -247,7 +247,7 @@ int adj_sep_split(const scatter_plan_s* p, int64_t tiles, int64_t n_ksteps, size
 }  // namespace
 
 bool adjoint_sep_applicable(const scatter_plan_s* p) {
-  return p->path == SCATTER_PATH_SEPARABLE && p->s_kind == SCATTER_S_GRID && p->batch == 1 && !p->d.ftab &&
+  return p->path == SCATTER_PATH_SEPARABLE && p->s_kind == SCATTER_S_GRID && p->batch == 1 &&
          p->n_s > 0 && p->n_slots % kSepStep == 0;
 }
 

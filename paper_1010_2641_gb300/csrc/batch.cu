@@ -29,6 +29,7 @@ struct BatchArgs {
   const Segment* segs;
   const int32_t* chunk_seg_off;
   const float* coef;
+  const float2* ftab;   // Eq. 4 factor table [n_species][M], or null (form factors)
   const float* s_hi;
   const float* s_lo;  // rounding error of s_hi (double-float s of the exact-product phases)
   const double* S64;
@@ -83,8 +84,8 @@ __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
     }
     const int chunk = in.chunk0 + w.chunk;
     float2 tot[R];
-    // batches take no factor table; a long crystal takes the exact-product
-    // phases with s as a double-float
+    // a long crystal takes the exact-product phases with s as a double-float;
+    // an Eq. 4 table holds one factor per (type, point) of the whole batch
     bool ok;
     if (dev::phase_needs_exact(a.inst_bbox + 6 * w.inst, a.inst_shift + 3 * w.inst, a.smax)) {
       auto lo = [&](int r, float& x, float& y, float& z) {
@@ -96,11 +97,13 @@ __global__ void __launch_bounds__(THREADS) k_batch(const BatchArgs a) {
       };
       ok = chunk_sum_exact_halves<kModeList, R>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
                                                 a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, lo,
-                                                sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+                                                sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s,
+                                                w.p0 + tid, THREADS);
     } else {
       ok = chunk_sum<kModeList, R, false>(a.atom4, a.atom_lo, a.atom_w, a.segs, a.chunk_seg_off[chunk],
                                           a.chunk_seg_off[chunk + 1], a.coef, in.H, a.inv4a2, sx, sy, sz, sx, sy, sz,
-                                          sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, nullptr, 1, 0, 0);
+                                          sh_atom, sh_lo, sh_w, sh_bar, k, tot, a.status, a.ftab, a.n_s, w.p0 + tid,
+                                          THREADS);
     }
     if (!ok) return;
     const int64_t M_b = in.s_end - in.s_begin;
@@ -301,6 +304,7 @@ scatter_status enqueue_batch_kernels(scatter_plan_t p, float2* amp, float* inten
   a.segs = p->d.segs;
   a.chunk_seg_off = p->d.chunk_seg_off;
   a.coef = p->d.coef;
+  a.ftab = p->d.ftab;
   a.s_hi = p->d.s_hi;
   a.s_lo = p->d.s_lo;
   a.S64 = p->d.S64;

@@ -113,7 +113,6 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
   if (pr->factor_table) {
     if (pr->s_kind == SCATTER_S_GID_GRID)
       return fail(SCATTER_ERR_UNSUPPORTED, "a factor table needs a LIST or GRID plan (one factor per point)");
-    if (pr->batch > 1) return fail(SCATTER_ERR_UNSUPPORTED, "a factor table needs a single instance");
     const int64_t M = pr->s_kind == SCATTER_S_LIST ? pr->n_s : pr->n_axis[0] * pr->n_axis[1] * pr->n_axis[2];
     for (int64_t i = 0; i < 2 * M * (int64_t)pr->n_species; ++i)
       if (!std::isfinite(pr->factor_table[i]))
