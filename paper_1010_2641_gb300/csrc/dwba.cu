@@ -37,8 +37,9 @@ constexpr int kDwbaR = 4;          // alpha_f points per thread
 constexpr int kDwbaWarps = 8;      // 8 warps x 4 = 32 alpha_f per CTA
 constexpr int kDwbaThreads = 32 * kDwbaWarps;
 constexpr int kAfBlock = kDwbaR * kDwbaWarps;  // 32
-// stage: Z table tile, atom records, position rounding errors (exact instance), weights
-constexpr size_t kDwbaStageBytes = (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16 + kDwbaTile * 16 + kDwbaTile * 4;
+// stage: Z table tile (occupancy folded in), atom records, position rounding
+// errors (exact instance)
+constexpr size_t kDwbaStageBytes = (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16 + kDwbaTile * 16;
 constexpr size_t kDwbaSmem = 2 * kDwbaStageBytes;
 
 struct DwbaArgs {
@@ -70,10 +71,12 @@ struct DwbaArgs {
   unsigned* status;
 };
 
-// Z table of the call: Z1, Z2 for every slot and alpha_f (padded to 32).
+// Z table of the call: w Z1, w Z2 for every slot and alpha_f (padded to 32),
+// the atom's occupancy folded in.
 __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __restrict__ atom_lo,
-                              const float* __restrict__ sz, const float* __restrict__ sz_lo, int64_t n_slots,
-                              int64_t n_af, int64_t n_afb, float4* __restrict__ ztab) {
+                              const float* __restrict__ atom_w, const float* __restrict__ sz,
+                              const float* __restrict__ sz_lo, int64_t n_slots, int64_t n_af, int64_t n_afb,
+                              float4* __restrict__ ztab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = n_afb * n_slots * kAfBlock;
   if (i >= total) return;
@@ -91,7 +94,8 @@ __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __
   float s1, c1, s2, c2;
   sincospif(2.0f * (dev::frac_of_product2(sz[af], sz_lo[af], z) + sz[af] * ez), &s1, &c1);
   sincospif(2.0f * (dev::frac_of_product2(sz[n_af + af], sz_lo[n_af + af], z) + sz[n_af + af] * ez), &s2, &c2);
-  ztab[i] = make_float4(c1, s1, c2, s2);
+  const float w = atom_w[slot];  // the occupancy rides in the table: w Z1, w Z2
+  ztab[i] = make_float4(w * c1, w * s1, w * c2, w * s2);
 }
 
 // Two FP32 values in one 64-bit register pair, for the packed f32x2 FMA.
@@ -117,9 +121,9 @@ __device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long 
 // rounding errors restored and s_h, s_k as double-floats (shl, skl their low
 // parts; long crystals).
 template <bool EXACT>
-__device__ __forceinline__ void dwba_tile_products(const float4* zs, const float4* as, const float4* es,
-                                                   const float* ws, int cnt, int af_l0, float sh, float sk, float shl,
-                                                   float skl, float (&acc)[kDwbaR][8]) {
+__device__ __forceinline__ void dwba_tile_products(const float4* zs, const float4* as, const float4* es, int cnt,
+                                                   int af_l0, float sh, float sk, float shl, float skl,
+                                                   float (&acc)[kDwbaR][8]) {
   unsigned long long pk[kDwbaR][4];  // (P1, R1), (T1, Q1), (P2, R2), (T2, Q2)
 #pragma unroll
   for (int r = 0; r < kDwbaR; ++r)
@@ -128,7 +132,6 @@ __device__ __forceinline__ void dwba_tile_products(const float4* zs, const float
 #pragma unroll 2
   for (int j = 0; j < cnt; ++j) {
     const float4 at = as[j];
-    const float w = ws[j];
     float f;
     if (EXACT) {
       const float4 e = es[j];  // the positions' FP32 rounding errors
@@ -137,9 +140,8 @@ __device__ __forceinline__ void dwba_tile_products(const float4* zs, const float
     } else {
       f = dev::frac_rn(fmaf(sk, at.y, fmaf(sh, at.x, at.w)));
     }
-    float sn, cs;
-    dev::sincos_cycles_mufu(f, &sn, &cs);
-    const float er = w * cs, ei = w * sn;
+    float er, ei;  // E / w (the table carries w)
+    dev::sincos_cycles_mufu(f, &ei, &er);
     const unsigned long long er2 = pack2(er, er), ei2 = pack2(ei, ei);
     const float4* zr = zs + j * kAfBlock + af_l0;
 #pragma unroll
@@ -188,9 +190,6 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
   auto stage_e = [&](int s) {
     return reinterpret_cast<float4*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 16);
   };
-  auto stage_w = [&](int s) {
-    return reinterpret_cast<float*>(smem + s * kDwbaStageBytes + (size_t)kDwbaTile * kAfBlock * 16 + kDwbaTile * 32);
-  };
 
   const int seg_lo = a.chunk_seg_off[chunk], seg_hi = a.chunk_seg_off[chunk + 1];
   if (tid == 0) {
@@ -206,11 +205,10 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
     if (l_seg >= seg_hi) return;
     const int64_t end = a.segs[l_seg].end;
     const int cnt = (int)dev::min64(kDwbaTile, end - l_begin);
-    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * (kAfBlock * 16u + (EXACT ? 36u : 20u)));
+    dev::mbar_arrive_expect_tx(&sh_bar[st], (uint32_t)cnt * (kAfBlock * 16u + (EXACT ? 32u : 16u)));
     dev::bulk_g2s(stage_z(st), zbase + l_begin * kAfBlock, (uint32_t)cnt * kAfBlock * 16u, &sh_bar[st]);
     dev::bulk_g2s(stage_a(st), a.atom4 + l_begin, (uint32_t)cnt * 16u, &sh_bar[st]);
     if (EXACT) dev::bulk_g2s(stage_e(st), a.atom_lo + l_begin, (uint32_t)cnt * 16u, &sh_bar[st]);
-    dev::bulk_g2s(stage_w(st), a.atom_w + l_begin, (uint32_t)cnt * 4u, &sh_bar[st]);
     l_begin += cnt;
     if (l_begin >= end && ++l_seg < seg_hi) l_begin = a.segs[l_seg].begin;
   };
@@ -242,8 +240,7 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     if (ok) {
-      dwba_tile_products<EXACT>(stage_z(st), stage_a(st), stage_e(st), stage_w(st), cnt, af_l0, sh, sk, shl, skl,
-                                acc);
+      dwba_tile_products<EXACT>(stage_z(st), stage_a(st), stage_e(st), cnt, af_l0, sh, sk, shl, skl, acc);
     }
     // beams of the tile: E Z1, E Z2, E conj(Z2), E conj(Z1)
 #pragma unroll
@@ -506,9 +503,9 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   const int64_t n_afb = (n_af + kAfBlock - 1) / kAfBlock;
   if (p->n_slots > 0) {
     const int64_t total = n_afb * p->n_slots * kAfBlock;
-    k_dwba_ztable<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p->d.atom4, p->d.atom_lo, p->d.gid_sz,
-                                                                    p->d.gid_sz_lo, p->n_slots, n_af, n_afb,
-                                                                    p->d.ztab);
+    k_dwba_ztable<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p->d.atom4, p->d.atom_lo, p->d.atom_w,
+                                                                    p->d.gid_sz, p->d.gid_sz_lo, p->n_slots, n_af,
+                                                                    n_afb, p->d.ztab);
     p->last_launches += 1;
   }
   DwbaArgs a{};
