@@ -14,6 +14,8 @@ Every function below follows the paper's definitions:
   fresnel      substrate reflection/transmission (Section 3, pynx.gid)
   dwba         four-beam grazing-incidence sum (Section 4.3; the formula is a
                reading, the paper prints none)
+  dwba_buried  the same geometry for an object inside the substrate: one
+               transmitted beam, refracted and attenuated (a reading too)
   loss_grad    L = sum (|A|^2 - I_obs)^2 and its analytic gradient
   fd_grad      central finite differences of L (a second route to the gradient)
   loss_grad_table  L and the analytic gradient of Eq. 4 (block origins, F fixed)
@@ -64,6 +66,7 @@ def _load():
         lib.oracle_fft_approx.argtypes = [i64, P, P, P, i32, P, f64, P, f64, P, i64, P, P]
         lib.oracle_fresnel.argtypes = [f64, f64, f64, P, P]
         lib.oracle_dwba.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
+        lib.oracle_dwba_buried.argtypes = [i64, P, P, P, i32, P, f64, f64, f64, f64, f64, i64, P, P]
         lib.oracle_loss_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, P, P]
         lib.oracle_fd_grad.argtypes = [i64, P, P, P, i32, P, f64, i64, P, P, i64, P, f64, P]
         lib.oracle_loss_grad_table.argtypes = [i64, P, P, P, i32, P, i64, P, P, P, P]
@@ -171,6 +174,19 @@ def dwba(xyz, pts, coef, lattice_a, wavelength, alpha_i, delta, beta, species=No
     _load().oracle_dwba(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
                         float(lattice_a), float(wavelength), float(alpha_i), float(delta), float(beta),
                         pts.shape[0], _ptr(pts), _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def dwba_buried(xyz, pts, coef, lattice_a, wavelength, alpha_i, delta, beta, species=None, occ=None) -> np.ndarray:
+    """Grazing-incidence amplitude of an object buried in the substrate
+    (z <= 0): one transmitted beam, T_i T_f, refracted and attenuated in the
+    medium, at points (h, k, alpha_f) [M,3]."""
+    xyz, sp, w, coef = _atoms(xyz, species, occ, coef)
+    pts = _f64(pts, 3)
+    out = np.zeros((pts.shape[0], 2))
+    _load().oracle_dwba_buried(xyz.shape[0], _ptr(xyz), _ptr(sp), _ptr(w), coef.shape[0], _ptr(coef),
+                               float(lattice_a), float(wavelength), float(alpha_i), float(delta), float(beta),
+                               pts.shape[0], _ptr(pts), _ptr(out))
     return out[:, 0] + 1j * out[:, 1]
 
 

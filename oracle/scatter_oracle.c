@@ -171,8 +171,9 @@ void oracle_fft_approx(int64_t n_atoms, const double* xyz, const int32_t* specie
  *                                      the field decays into the substrate)
  *   R = (k_z - k_z') / (k_z + k_z'),  T = 1 + R.
  */
-void oracle_fresnel(double alpha, double delta, double beta, double* R, double* T) {
-  const double kz = sin(alpha);
+/* sin of the refracted grazing angle in a medium of index n = 1 - delta + i beta:
+ * q = sqrt(n^2 - cos^2 alpha), principal branch (Im q >= 0), so that k_z' = k q. */
+static void refracted_sin(double alpha, double delta, double beta, double* q_re, double* q_im) {
   /* n^2 = (1 - delta)^2 - beta^2 + 2 i beta (1 - delta) */
   const double n2_re = (1.0 - delta) * (1.0 - delta) - beta * beta;
   const double n2_im = 2.0 * beta * (1.0 - delta);
@@ -183,6 +184,14 @@ void oracle_fresnel(double alpha, double delta, double beta, double* R, double* 
   double k_re = sqrt(0.5 * (mod + z_re));
   double k_im = sqrt(fmax(0.0, 0.5 * (mod - z_re)));
   if (z_im < 0) k_im = -k_im;
+  *q_re = k_re;
+  *q_im = k_im;
+}
+
+void oracle_fresnel(double alpha, double delta, double beta, double* R, double* T) {
+  const double kz = sin(alpha);
+  double k_re, k_im;
+  refracted_sin(alpha, delta, beta, &k_re, &k_im);
   /* R = (kz - k') / (kz + k') */
   const double nr = kz - k_re, ni = -k_im;
   const double dr = kz + k_re, di = k_im;
@@ -279,6 +288,62 @@ static void grad_one_atom(const double* r, double w, const double* coef_s, doubl
   out[0] = -2.0 * kPi * gx;
   out[1] = -2.0 * kPi * gy;
   out[2] = -2.0 * kPi * gz;
+}
+
+/*
+ * Grazing incidence on an object buried in the substrate (the reading of the
+ * buried case of Section 4.3, where the paper names the transmission
+ * coefficients beside the reflection ones and prints no formula): the
+ * substrate fills z < 0 below a flat surface at z = 0 (lattice units), the
+ * atoms lie inside it (z <= 0), and the substrate has no lower interface, so
+ * inside it there is one incident wave, transmitted with T_i = T(alpha_i), and
+ * one wave towards the detector, transmitted with T_f = T(alpha_f).  Both are
+ * refracted: with q = sqrt(n^2 - cos^2 alpha) (Im q >= 0) the in-medium
+ * momentum transfer along z is (a / lambda)(q_i + q_f), and both waves decay
+ * with depth, e^{(2 pi a / lambda)(Im q_i + Im q_f) z} for z <= 0.  So
+ *   A(h, k, alpha_f) = T_i T_f sum_s f_s(|S_1|) sum_{j in s} w_j
+ *                        exp(2 i pi (h x_j + k y_j + sigma z_j)),
+ *   sigma = (a / lambda)(conj(q_i) + conj(q_f)),
+ * with f at the vacuum beam S_1 = (h, k, (a / lambda)(sin a_i + sin a_f)).
+ * With delta = beta = 0, T = 1 and sigma = S_1z: the kinematic sum at S_1.
+ *
+ *  pts  [n_pts][3] = (h, k, alpha_f in rad)     A out [n_pts][2]
+ */
+void oracle_dwba_buried(int64_t n_atoms, const double* xyz, const int32_t* species,
+                        const double* occ, int32_t n_species, const double* coef,
+                        double lattice_a, double wavelength, double alpha_i, double delta,
+                        double beta, int64_t n_pts, const double* pts, double* A) {
+  (void)n_species;
+  double Ri[2], Ti[2], qi_re, qi_im;
+  oracle_fresnel(alpha_i, delta, beta, Ri, Ti);
+  refracted_sin(alpha_i, delta, beta, &qi_re, &qi_im);
+  const double scale = lattice_a / wavelength;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t m = 0; m < n_pts; ++m) {
+    const double h = pts[3 * m], k = pts[3 * m + 1], af = pts[3 * m + 2];
+    double Rf[2], Tf[2], qf_re, qf_im;
+    oracle_fresnel(af, delta, beta, Rf, Tf);
+    refracted_sin(af, delta, beta, &qf_re, &qf_im);
+    const double sig_re = scale * (qi_re + qf_re), sig_im = -scale * (qi_im + qf_im);
+    const double S1[3] = {h, k, scale * (sin(alpha_i) + sin(af))};
+    const double q = s_norm(S1, lattice_a);
+    double are = 0.0, aim = 0.0;
+    for (int64_t j = 0; j < n_atoms; ++j) {
+      const double* r = xyz + 3 * j;
+      const double phase = 2.0 * kPi * (h * r[0] + k * r[1] + sig_re * r[2]);
+      const double damp = exp(-2.0 * kPi * sig_im * r[2]);
+      const double c = damp * cos(phase), s = damp * sin(phase);
+      const double w = occ ? occ[j] : 1.0;
+      double fr, fi;
+      oracle_form_factor(coef + ORACLE_NCOEF * (species ? species[j] : 0), q, &fr, &fi);
+      are += w * (fr * c - fi * s);
+      aim += w * (fr * s + fi * c);
+    }
+    /* T_i T_f times the sum */
+    const double tr = Ti[0] * Tf[0] - Ti[1] * Tf[1], ti = Ti[0] * Tf[1] + Ti[1] * Tf[0];
+    A[2 * m] = tr * are - ti * aim;
+    A[2 * m + 1] = tr * aim + ti * are;
+  }
 }
 
 /*

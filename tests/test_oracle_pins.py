@@ -286,6 +286,64 @@ def test_dwba_four_beams():
         assert abs(A[m] - tot) < 1e-9 * max(1.0, abs(tot))
 
 
+def test_buried_dwba_without_substrate_is_the_kinematic_sum():
+    """delta = beta = 0: T = 1, no refraction: the buried reading reduces to
+    Eq. 2 at the vacuum beam S_1 (atoms below the surface plane)."""
+    rng = np.random.default_rng(23)
+    xyz = rng.uniform(-5, 5, (50, 3))
+    xyz[:, 2] = -np.abs(xyz[:, 2])
+    sp = rng.integers(0, 2, 50).astype(np.int32)
+    coef = W.si_ge_species()
+    lam, ai = W.WAVELENGTH_10KEV, W.GID_ALPHA_I
+    pts = np.stack([rng.uniform(3.8, 4.1, 25), rng.uniform(-0.1, 0.1, 25), np.radians(rng.uniform(0.05, 1, 25))], 1)
+    A = oracle.dwba_buried(xyz, pts, coef, A_LAT, lam, ai, 0.0, 0.0, species=sp)
+    S1 = np.stack([_kin_S(p[0], p[1], ai, p[2], lam, A_LAT, False, False) for p in pts])
+    ref = oracle.amplitude(xyz, S1, coef, A_LAT, species=sp)
+    # sqrt(1 - cos^2 a) against sin a at a ~ 4e-3 rad: ~1e-11 relative in sigma
+    assert np.allclose(A, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+def test_buried_dwba_surface_atom_takes_both_transmission_coefficients():
+    """One atom in the surface plane: |A| = |T_i T_f f|, with T from the
+    textbook s-polarised transmission 2 k_z / (k_z + k_z') (not 1 + R)."""
+    lam, ai, d, b = W.WAVELENGTH_10KEV, W.GID_ALPHA_I, 2e-5, 4e-7
+    xyz = np.array([[0.3, -0.7, 0.0]])
+    coef = W.unit_species()[None]
+    pts = np.array([[4.0, 0.0, np.radians(a)] for a in (0.05, 0.15, 0.26, 0.5, 1.0)])
+    A = oracle.dwba_buried(xyz, pts, coef, A_LAT, lam, ai, d, b)
+    n = 1 - d + 1j * b
+
+    def T(alpha):
+        kz = np.sin(alpha)
+        kzp = np.sqrt(n * n - np.cos(alpha) ** 2)
+        return 2 * kz / (kz + kzp)
+
+    for m, p in enumerate(pts):
+        assert abs(abs(A[m]) - abs(T(ai) * T(p[2]))) < 1e-12
+        phase = np.exp(2j * np.pi * (p[0] * xyz[0, 0] + p[1] * xyz[0, 1]))
+        assert abs(A[m] - T(ai) * T(p[2]) * phase) < 1e-12
+
+
+def test_buried_dwba_evanescent_decay_below_the_critical_angle():
+    """beta = 0 and both angles below the critical angle sqrt(2 delta): total
+    reflection, the waves are evanescent, and an atom at depth D scatters
+    |T_i T_f| exp(-(2 pi a / lambda)(kappa_i + kappa_f) D) with kappa =
+    sqrt(cos^2 a - (1 - delta)^2) (Snell's law with cos a > n)."""
+    lam, d = W.WAVELENGTH_10KEV, 1e-5
+    ac = np.sqrt(2 * d)
+    ai = 0.5 * ac
+    coef = W.unit_species()[None]
+    pts = np.array([[4.0, 0.0, f * ac] for f in (0.3, 0.6, 0.9)])
+    _, Ti = fresnel_textbook(ai, d, 0.0)
+    for D in (0.0, 3.0, 40.0, 250.0):
+        A = oracle.dwba_buried(np.array([[0.0, 0.0, -D]]), pts, coef, A_LAT, lam, ai, d, 0.0)
+        for m, p in enumerate(pts):
+            _, Tf = fresnel_textbook(p[2], d, 0.0)
+            kap = [np.sqrt(np.cos(a) ** 2 - (1 - d) ** 2) for a in (ai, p[2])]
+            want = abs(Ti * Tf) * np.exp(-2 * np.pi * A_LAT / lam * (kap[0] + kap[1]) * D)
+            assert abs(abs(A[m]) - want) <= 1e-10 * abs(Ti * Tf)
+
+
 # ----------------------------------------------------------------------------
 # Misfit gradient: two routes and closed forms
 # ----------------------------------------------------------------------------
