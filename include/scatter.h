@@ -145,6 +145,20 @@ typedef struct scatter_problem {
    * per point does not define the sum).  Copied at plan time.  NULL: the
    * form factors of `species`.                                            */
   const double* factor_table;
+
+  /* GID_GRID only: where the scatterer sits (Section 4.3 names reflection
+   * and transmission by the substrate):
+   *   0  on the substrate, in vacuum (z >= 0 above the surface plane z = 0):
+   *      four beams, direct and reflected in and out, W = (1, R_i, R_f,
+   *      R_i R_f);
+   *   1  buried in the substrate (z <= 0, lattice units below the surface
+   *      plane z = 0; the substrate has no lower interface): one beam
+   *      transmitted in and out, W = T_i T_f, refracted and attenuated in
+   *      the medium: exp(2 i pi (h x + k y + sigma z)), sigma =
+   *      (a / lambda)(conj q_i + conj q_f), q = sqrt(n^2 - cos^2 alpha),
+   *      f at the vacuum beam S_1.  Generic and FP64 paths (the separable
+   *      path's formed rows are unit-modulus phases).                      */
+  int32_t gid_mode;
 } scatter_problem;
 
 /* Plan options.  Zero-initialised options mean "automatic". */

@@ -51,7 +51,9 @@ class Plan:
     axes : three 1-D arrays h, k, l (grid sampling; GID: h, k, alpha_f).
     atom_species : [N] int (or None: all species 0); n_atoms : N.
     center : reference reflection H (integers) or None (automatic).
-    gid : dict(wavelength=, alpha_i=, delta=, beta=) for grazing incidence.
+    gid : dict(wavelength=, alpha_i=, delta=, beta=[, buried=True]) for grazing
+        incidence; buried=True: the object lies in the substrate below the
+        surface plane z = 0 (one transmitted beam), else on it (four beams).
     atom_off, s_off : batch CSR offsets (lists only).
     factor_table : [n_species, M] complex (Eq. 4, blocks of atoms): the
         "species" are block types with structure factors F_t(S_m) given per
@@ -115,6 +117,7 @@ class Plan:
             pr.alpha_i = float(gid["alpha_i"])
             pr.delta = float(gid.get("delta", 0.0))
             pr.beta = float(gid.get("beta", 0.0))
+            pr.gid_mode = 1 if gid.get("buried", False) else 0
         pr.batch = 1
         if atom_off is not None:
             ao = np.ascontiguousarray(np.asarray(atom_off, dtype=np.int64))

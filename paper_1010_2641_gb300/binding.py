@@ -66,6 +66,7 @@ class scatter_problem(ctypes.Structure):
         ("atom_off", c_void_p),
         ("s_off", c_void_p),
         ("factor_table", c_void_p),
+        ("gid_mode", c_int32),
     ]
 
 

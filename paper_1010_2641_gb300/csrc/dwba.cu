@@ -56,6 +56,8 @@ struct DwbaArgs {
   const double* axis64;    // [n0 | n1 | n_af]: h, k, alpha_f
   const float* gid_sz;     // [2][n_af] Sz1, Sz2 (r.l.u.)
   const double* gid_sz64;  // [2][n_af]
+  const float* gid_szf;    // [4][n_af] S_z of each beam's form factor
+  const double* gid_sz64_im;  // [n_af] Im sigma of a buried object's beam, 0 on the substrate
   const float2* gid_w;     // [4][n_af]
   int64_t n0, n1, n_af;
   float H[3];
@@ -75,8 +77,8 @@ struct DwbaArgs {
 // the atom's occupancy folded in.
 __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __restrict__ atom_lo,
                               const float* __restrict__ atom_w, const float* __restrict__ sz,
-                              const float* __restrict__ sz_lo, int64_t n_slots, int64_t n_af, int64_t n_afb,
-                              float4* __restrict__ ztab) {
+                              const float* __restrict__ sz_lo, const float* __restrict__ sz_im, int64_t n_slots,
+                              int64_t n_af, int64_t n_afb, float4* __restrict__ ztab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = n_afb * n_slots * kAfBlock;
   if (i >= total) return;
@@ -94,8 +96,12 @@ __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __
   float s1, c1, s2, c2;
   sincospif(2.0f * (dev::frac_of_product2(sz[af], sz_lo[af], z) + sz[af] * ez), &s1, &c1);
   sincospif(2.0f * (dev::frac_of_product2(sz[n_af + af], sz_lo[n_af + af], z) + sz[n_af + af] * ez), &s2, &c2);
-  const float w = atom_w[slot];  // the occupancy rides in the table: w Z1, w Z2
-  ztab[i] = make_float4(w * c1, w * s1, w * c2, w * s2);
+  // the occupancy rides in the table: w Z1, w Z2; a buried object's beam is
+  // attenuated in the medium, |Z1| = exp(-2 pi Im(sigma) z') (Im sz = 0 otherwise)
+  const float w = atom_w[slot];
+  const float w1 = w * expf(-6.28318530717958647692f * sz_im[af] * (z + ez));
+  const float w2 = w * expf(-6.28318530717958647692f * sz_im[n_af + af] * (z + ez));
+  ztab[i] = make_float4(w1 * c1, w1 * s1, w2 * c2, w2 * s2);
 }
 
 // Two FP32 values in one 64-bit register pair, for the packed f32x2 FMA.
@@ -265,15 +271,19 @@ __global__ void __launch_bounds__(kDwbaThreads) k_dwba(const DwbaArgs a) {
 #pragma unroll
       for (int r = 0; r < kDwbaR; ++r) {
         const int64_t af = af0 + r < a.n_af ? af0 + r : a.n_af - 1;
-        const float sz1 = a.gid_sz[af], sz2 = a.gid_sz[a.n_af + af];
-        const float szt[4] = {sz1, sz2, -sz2, -sz1};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const float s2 = (Sx * Sx + Sy * Sy + szt[t] * szt[t]) * a.inv4a2;
+          const float szf = a.gid_szf[t * a.n_af + af];
+          const float s2 = (Sx * Sx + Sy * Sy + szf * szf) * a.inv4a2;
           float2 wf = dev::cmul(a.gid_w[t * a.n_af + af], dev::form_factor(cf, s2));
           if (shifted) {
             const double z64 = (t == 0 || t == 3 ? a.gid_sz64[af] : a.gid_sz64[a.n_af + af]) * (t < 2 ? 1.0 : -1.0);
             wf = dev::cmul(dev::shift_phase(a.axis64[i_h] - a.H64[0], a.axis64[a.n0 + i_k] - a.H64[1], z64, tt), wf);
+            if (t == 0) {  // a buried object's attenuation over the centring shift
+              const float att = (float)exp(-6.283185307179586 * a.gid_sz64_im[af] * tt[2]);
+              wf.x *= att;
+              wf.y *= att;
+            }
           }
           const float2 v = dev::cmul(wf, seg[r][t]);
           tot[r].x += v.x;
@@ -329,6 +339,7 @@ __global__ void __launch_bounds__(128) k_f64_gid(const double* __restrict__ xyz,
                                                  const int32_t* __restrict__ slot_src, const Segment* __restrict__ segs,
                                                  int n_segs, const double* __restrict__ coef64,
                                                  const double* __restrict__ axis64, const double* __restrict__ sz64,
+                                                 const double* __restrict__ szf64, const double* __restrict__ sz64_im,
                                                  const double2* __restrict__ w64, int64_t n0, int64_t n1,
                                                  int64_t n_af, double inv4a2, float2* out_amp, float* out_int) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,7 +350,11 @@ __global__ void __launch_bounds__(128) k_f64_gid(const double* __restrict__ xyz,
   const double szt[4] = {sz1, sz2, -sz2, -sz1};
   double are = 0.0, aim = 0.0;
   for (int t = 0; t < 4; ++t) {
-    const double s2 = (h * h + kk * kk + szt[t] * szt[t]) * inv4a2;
+    const double2 W = w64[t * n_af + af];
+    if (W.x == 0.0 && W.y == 0.0) continue;  // a buried object: one beam
+    const double szf = szf64[t * n_af + af];
+    const double s2 = (h * h + kk * kk + szf * szf) * inv4a2;
+    const double im = t == 0 ? sz64_im[af] : 0.0;
     double tr_all = 0.0, ti_all = 0.0;
     for (int g = 0; g < n_segs; ++g) {
       const Segment sg = segs[g];
@@ -356,13 +371,13 @@ __global__ void __launch_bounds__(128) k_f64_gid(const double* __restrict__ xyz,
         const double w = occ ? (double)occ[j] : 1.0;
         double sn, cs;
         sincospi(2.0 * (h * r[0] + kk * r[1] + szt[t] * r[2]), &sn, &cs);
-        tr += w * cs;
-        ti += w * sn;
+        const double wa = im != 0.0 ? w * exp(-2.0 * 3.14159265358979323846 * im * r[2]) : w;
+        tr += wa * cs;
+        ti += wa * sn;
       }
       tr_all += fr * tr - fi * ti;
       ti_all += fr * ti + fi * tr;
     }
-    const double2 W = w64[t * n_af + af];
     are += W.x * tr_all - W.y * ti_all;
     aim += W.x * ti_all + W.y * tr_all;
   }
@@ -412,6 +427,14 @@ std::complex<double> fresnel_r(double alpha, double delta, double beta) {
   return (kz - kt) / (kz + kt);
 }
 
+// sin of the refracted angle in the substrate, q = sqrt(n^2 - cos^2 alpha)
+// (principal branch: Im q >= 0, the field decays into the substrate)
+std::complex<double> refracted_sin(double alpha, double delta, double beta) {
+  const std::complex<double> n(1.0 - delta, beta);
+  const double ca = std::cos(alpha);
+  return std::sqrt(n * n - ca * ca);
+}
+
 }  // namespace
 
 int dwba_blocks_per_sm() {
@@ -438,19 +461,37 @@ scatter_status prepare_gid(scatter_plan_s* p) {
   const int64_t n_af = p->n_axis[2];
   const double scale = p->lattice_a / p->wavelength;
   const std::complex<double> Ri = fresnel_r(p->alpha_i, p->delta, p->beta);
-  std::vector<double> sz64(2 * n_af);
-  std::vector<float> sz(2 * n_af), sz_lo(2 * n_af);
+  const std::complex<double> qi = refracted_sin(p->alpha_i, p->delta, p->beta);
+  const bool buried = p->gid_mode == 1;
+  std::vector<double> sz64(2 * n_af), szf64(4 * n_af), sz64_im(n_af, 0.0);
+  std::vector<float> sz(2 * n_af), sz_lo(2 * n_af), sz_im(2 * n_af, 0.f), szf(4 * n_af);
   std::vector<double2> w64(4 * n_af);
   std::vector<float2> w32(4 * n_af);
   for (int64_t i = 0; i < n_af; ++i) {
     const double af = p->axis_host[2][i];
-    sz64[i] = scale * (std::sin(p->alpha_i) + std::sin(af));
-    sz64[n_af + i] = scale * (std::sin(af) - std::sin(p->alpha_i));
+    const double s1 = scale * (std::sin(p->alpha_i) + std::sin(af)), s2 = scale * (std::sin(af) - std::sin(p->alpha_i));
     const std::complex<double> Rf = fresnel_r(af, p->delta, p->beta);
-    const std::complex<double> W[4] = {1.0, Ri, Rf, Ri * Rf};
+    std::complex<double> W[4] = {1.0, Ri, Rf, Ri * Rf};
+    double szf_t[4] = {s1, s2, -s2, -s1};
+    if (!buried) {
+      sz64[i] = s1;
+      sz64[n_af + i] = s2;
+    } else {
+      // one beam, transmitted in and out, refracted and attenuated in the medium
+      const std::complex<double> sigma = scale * (std::conj(qi) + std::conj(refracted_sin(af, p->delta, p->beta)));
+      sz64[i] = sigma.real();
+      sz64[n_af + i] = 0.0;
+      sz64_im[i] = sigma.imag();
+      sz_im[i] = (float)sigma.imag();
+      W[0] = (1.0 + Ri) * (1.0 + Rf);
+      W[1] = W[2] = W[3] = 0.0;
+      szf_t[1] = szf_t[2] = szf_t[3] = 0.0;
+    }
     for (int t = 0; t < 4; ++t) {
       w64[t * n_af + i] = make_double2(W[t].real(), W[t].imag());
       w32[t * n_af + i] = make_float2((float)W[t].real(), (float)W[t].imag());
+      szf64[t * n_af + i] = szf_t[t];
+      szf[t * n_af + i] = (float)szf_t[t];
     }
     p->s_max[2] = std::max(p->s_max[2], std::fabs(sz64[i]));
     for (int64_t q : {i, n_af + i}) {
@@ -468,6 +509,14 @@ scatter_status prepare_gid(scatter_plan_s* p) {
   p->gid_sz_host = sz64;
   if ((e = up((void**)&p->d.gid_sz, sz.data(), sz.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "gid");
   if ((e = up((void**)&p->d.gid_sz_lo, sz_lo.data(), sz_lo.size() * sizeof(float))) != cudaSuccess)
+    return cuda_status(e, "gid");
+  if ((e = up((void**)&p->d.gid_sz_im, sz_im.data(), sz_im.size() * sizeof(float))) != cudaSuccess)
+    return cuda_status(e, "gid");
+  if ((e = up((void**)&p->d.gid_szf, szf.data(), szf.size() * sizeof(float))) != cudaSuccess)
+    return cuda_status(e, "gid");
+  if ((e = up((void**)&p->d.gid_szf64, szf64.data(), szf64.size() * sizeof(double))) != cudaSuccess)
+    return cuda_status(e, "gid");
+  if ((e = up((void**)&p->d.gid_sz64_im, sz64_im.data(), sz64_im.size() * sizeof(double))) != cudaSuccess)
     return cuda_status(e, "gid");
   if ((e = up((void**)&p->d.gid_sz64, sz64.data(), sz64.size() * sizeof(double))) != cudaSuccess)
     return cuda_status(e, "gid");
@@ -504,8 +553,8 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   if (p->n_slots > 0) {
     const int64_t total = n_afb * p->n_slots * kAfBlock;
     k_dwba_ztable<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p->d.atom4, p->d.atom_lo, p->d.atom_w,
-                                                                    p->d.gid_sz, p->d.gid_sz_lo, p->n_slots, n_af,
-                                                                    n_afb, p->d.ztab);
+                                                                    p->d.gid_sz, p->d.gid_sz_lo, p->d.gid_sz_im,
+                                                                    p->n_slots, n_af, n_afb, p->d.ztab);
     p->last_launches += 1;
   }
   DwbaArgs a{};
@@ -522,6 +571,8 @@ scatter_status launch_dwba(scatter_plan_t p, float2* amp_out, float* int_out, cu
   a.axis64 = p->d.axis64;
   a.gid_sz = p->d.gid_sz;
   a.gid_sz64 = p->d.gid_sz64;
+  a.gid_szf = p->d.gid_szf;
+  a.gid_sz64_im = p->d.gid_sz64_im;
   a.gid_w = p->d.gid_w;
   a.n0 = p->n_axis[0];
   a.n1 = p->n_axis[1];
@@ -564,7 +615,8 @@ scatter_status launch_f64_gid(scatter_plan_t p, const double* xyz, const float* 
   const int64_t nb = (p->n_s + 127) / 128;
   timing_begin(p, st);
   k_f64_gid<<<(unsigned)nb, 128, 0, st>>>(xyz, occ, p->d.slot_src, p->d.segs, (int)p->segs.size(), p->d.coef64,
-                                          p->d.axis64, p->d.gid_sz64, p->d.gid_w64, p->n_axis[0], p->n_axis[1],
+                                          p->d.axis64, p->d.gid_sz64, p->d.gid_szf64, p->d.gid_sz64_im, p->d.gid_w64,
+                                          p->n_axis[0], p->n_axis[1],
                                           p->n_axis[2], 1.0 / (4.0 * p->lattice_a * p->lattice_a), amp_out, int_out);
   timing_end(p, st);
   p->last_launches += 1;

@@ -90,6 +90,9 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
     if (!std::isfinite(pr->alpha_i) || !std::isfinite(pr->delta) || !std::isfinite(pr->beta) ||
         pr->delta < 0 || pr->beta < 0)
       return fail(SCATTER_ERR_INVALID_ARG, "invalid alpha_i/delta/beta");
+    if (pr->gid_mode != 0 && pr->gid_mode != 1) return fail(SCATTER_ERR_INVALID_ARG, "gid_mode must be 0 or 1");
+    if (pr->gid_mode == 1 && op && op->path == SCATTER_PATH_SEPARABLE)
+      return fail(SCATTER_ERR_UNSUPPORTED, "a buried object (gid_mode 1) runs on the generic or FP64 path");
   }
   if (pr->center_mode != 0 && pr->center_mode != 1)
     return fail(SCATTER_ERR_INVALID_ARG, "center_mode must be 0 or 1");
@@ -157,6 +160,7 @@ constexpr double kSepModelMargin = 4.0;
 // with the measured margin, stays within the caller's tolerance.
 bool auto_prefers_separable(const scatter_plan_s* p, const scatter_options* op) {
   if (p->batch != 1 || (p->s_kind != SCATTER_S_GRID && p->s_kind != SCATTER_S_GID_GRID)) return false;
+  if (p->gid_mode != 0) return false;  // a buried object: attenuated rows, generic path
   if (p->n_slots % 16) return false;
   const int64_t n0 = p->n_axis[0];
   const int64_t n12 = p->n_axis[1] * (p->s_kind == SCATTER_S_GID_GRID ? 4 * p->n_axis[2] : p->n_axis[2]);
@@ -287,6 +291,10 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.status);
   release(d.gid_sz);
   release(d.gid_sz_lo);
+  release(d.gid_sz_im);
+  release(d.gid_szf);
+  release(d.gid_szf64);
+  release(d.gid_sz64_im);
   release(d.gid_sz64);
   release(d.gid_w);
   release(d.gid_w64);
@@ -350,6 +358,7 @@ extern "C" scatter_status scatter_plan(const scatter_problem* pr, const scatter_
   p->alpha_i = pr->alpha_i;
   p->delta = pr->delta;
   p->beta = pr->beta;
+  p->gid_mode = pr->s_kind == SCATTER_S_GID_GRID ? pr->gid_mode : 0;
   p->use_graph = !(op && op->use_graph < 0);
   if (op && op->timing) {
     p->timing = true;

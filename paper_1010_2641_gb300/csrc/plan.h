@@ -114,6 +114,10 @@ struct DeviceBuffers {
   // grazing incidence (GID grids)
   float* gid_sz = nullptr;          // [2][n_af] Sz1, Sz2 r.l.u.
   float* gid_sz_lo = nullptr;       // [2][n_af] their FP32 rounding errors
+  float* gid_sz_im = nullptr;       // [2][n_af] Im of a buried object's S_z (0 on the substrate)
+  float* gid_szf = nullptr;         // [4][n_af] S_z of each beam's form factor (vacuum)
+  double* gid_szf64 = nullptr;      // [4][n_af]
+  double* gid_sz64_im = nullptr;    // [n_af] Im sigma of a buried object's beam (0 on the substrate)
   double* gid_sz64 = nullptr;       // [2][n_af]
   float2* gid_w = nullptr;          // [4][n_af] beam weights
   double2* gid_w64 = nullptr;       // [4][n_af]
@@ -170,6 +174,7 @@ struct scatter_plan_s {
   std::vector<int64_t> chunk_slots;              // slots per chunk (cost)
   scatter::Tiling tiling;
   double wavelength = 0, alpha_i = 0, delta = 0, beta = 0;
+  int gid_mode = 0;                              // 0: on the substrate (four beams), 1: buried (one beam)
   scatter::DeviceBuffers d;
   int64_t base_bytes = 0;                        // tables and backward workspace
   int64_t tiling_bytes = 0;                      // chunk tables and split-K partials

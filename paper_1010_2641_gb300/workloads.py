@@ -187,6 +187,14 @@ def truncated_pyramid(base_cells: int = 120, height_cells: int = 40, top_cells: 
     return Crystal(np.concatenate(parts), np.concatenate(spec), coef)
 
 
+def below_surface(c: Crystal, depth_cells: float) -> Crystal:
+    """The same crystal moved into the substrate: its top at depth_cells
+    below the surface plane z = 0 (every z <= -depth_cells)."""
+    xyz = c.xyz.copy()
+    xyz[:, 2] -= xyz[:, 2].max() + depth_cells
+    return Crystal(xyz, c.species.copy(), c.coef.copy(), c.occ)
+
+
 def gid_axes(n_h: int = 512, n_k: int = 512, n_af: int = 32):
     """Grazing-incidence map around in-plane (400): h in [3.80, 4.05],
     k in [-0.125, 0.125] (inclusive) and alpha_f = (i+1)/32 degrees."""

@@ -9,6 +9,7 @@ import __graft_entry__
 import oracle
 from closed_forms import rel_l2
 from paper_1010_2641_gb300 import api
+from paper_1010_2641_gb300 import binding as B
 from paper_1010_2641_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -137,3 +138,47 @@ def test_long_chain_takes_exact_phases(path, tol):
     err = rel_l2(A, ref)
     print(f"long DWBA chain ({path}): rel L2 {err:.1e}")
     assert err < tol
+
+
+# ---- an object buried in the substrate: one transmitted beam -----------------
+
+def buried_map(c, axes, path="generic", delta=W.GID_DELTA, beta=W.GID_BETA):
+    gid = dict(wavelength=LAM, alpha_i=W.GID_ALPHA_I, delta=delta, beta=beta, buried=True)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, gid=gid, path=path)
+    A = plan.amplitude(torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0"))
+    plan.check()
+    return A.cpu().numpy().astype(np.complex128), plan
+
+
+@pytest.mark.parametrize("path,tol", [("generic", 1e-4), ("fp64", 1e-6)])
+@pytest.mark.parametrize("beta", [W.GID_BETA, 0.0])
+def test_buried_island_vs_oracle(path, tol, beta):
+    """A small island 2 cells below the surface; exit angles cross the critical
+    angle (0.256 deg), where the transmitted waves turn evanescent (beta = 0:
+    pure decay with depth)."""
+    c = W.below_surface(small_island(), 2.0)
+    axes = [np.linspace(3.8, 4.05, 20), np.linspace(-0.125, 0.125, 18), np.deg2rad((np.arange(40) + 1) / 32)]
+    A, plan = buried_map(c, axes, path=path, beta=beta)
+    ref = oracle.dwba_buried(c.xyz, gid_points(axes), c.coef, A_LAT, LAM, W.GID_ALPHA_I, W.GID_DELTA, beta,
+                             species=c.species)
+    err = rel_l2(A, ref)
+    print(f"buried island ({path}, beta {beta:g}): rel L2 {err:.1e}")
+    assert err < tol
+
+
+def test_buried_without_substrate_is_the_kinematic_beam():
+    c = W.below_surface(small_island(), 1.0)
+    axes = [np.linspace(3.9, 4.0, 6), np.linspace(-0.02, 0.02, 5), np.deg2rad(np.linspace(0.1, 0.9, 8))]
+    A, _ = buried_map(c, axes, delta=0.0, beta=0.0)
+    P = gid_points(axes)
+    S1 = np.stack([P[:, 0], P[:, 1], A_LAT / LAM * (np.sin(W.GID_ALPHA_I) + np.sin(P[:, 2]))], 1)
+    assert rel_l2(A, oracle.amplitude(c.xyz, S1, c.coef, A_LAT, species=c.species)) < 1e-4
+
+
+def test_buried_plans_stay_off_the_tensor_cores():
+    c = W.below_surface(W.truncated_pyramid(base_cells=24, height_cells=8, top_cells=8), 1.0)
+    axes = list(W.gid_axes(48, 48, 32))
+    _, plan = buried_map(c, axes, path="auto")
+    assert plan.info()["path"] == B.SCATTER_PATH_GENERIC
+    with pytest.raises(B.ScatterError):
+        buried_map(c, axes, path="separable")
