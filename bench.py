@@ -168,7 +168,7 @@ def kernel_source_hash(files=GENERIC_SOURCES) -> str:
     return h.hexdigest()[:12]
 
 
-SEP_SOURCES = ("separable.cu", "sep_common.cuh", "device_common.cuh", "plan.h")
+SEP_SOURCES = ("separable.cu", "sep_pair.cu", "sep_common.cuh", "device_common.cuh", "plan.h")
 
 
 def profiled_traffic(name="generic_strained_sphere.md", files=GENERIC_SOURCES):
@@ -326,7 +326,9 @@ def run_gpu(args, rank, world, local_rank):
         achieved = executed / (t_kern * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None if args.grid else profiled_traffic("separable_strained_sphere.md", SEP_SOURCES),
-                "kernel": "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)",
+                "kernel": ("k_sep_pair (tcgen05.mma.cta_group::2 kind::f16, M=256 N=256 on a CTA pair, "
+                           "3 split products)" if os.environ.get("SCATTER_SEP_PAIR", "1") != "0" else
+                           "k_sep (tcgen05.mma kind::f16, M=128 N=256, 3 split products)"),
                 "kernel_ms": t_kern, "useful_tflops": useful / (t_kern * 1e-3) / 1e12,
                 "peak_basis": f"{basis} (f16 and bf16 share the dense tensor rate)"}
         # cross-check: this GPU's own f16 MMA rate (back-to-back tcgen05.mma, M=128 N=256, zero operands)
