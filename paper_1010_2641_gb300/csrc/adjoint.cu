@@ -338,6 +338,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
       sv[r] = szv[r] = 0.f;
     }
     if (ok) {
+      // two atoms per packed register pair: every operation of the recurrence
+      // is elementwise over the atoms, so one fma.rn.f32x2 does two atoms'
+      // FMA (the same rounding as fmaf); the point's values are broadcast
+      using u64 = unsigned long long;
+      constexpr int kP = kAdjRA / 2;
+      u64 wr2[kP], wi2[kP], nwi2[kP], sv2[kP], szv2[kP];
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        wr2[p] = dev::pack2(wr[2 * p], wr[2 * p + 1]);
+        wi2[p] = dev::pack2(wi[2 * p], wi[2 * p + 1]);
+        nwi2[p] = dev::pack2(-wi[2 * p], -wi[2 * p + 1]);
+        sv2[p] = szv2[p] = 0ull;
+      }
+      const u64 one2 = dev::pack2(1.f, 1.f), zero2 = 0ull;
       const float4* sv4 = sh_s[st];
       for (int jb = 0; jb < cnt; jb += kReseed) {
         // exact exponential at the first point of every 64
@@ -345,20 +359,32 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
 #pragma unroll
         for (int r = 0; r < kAdjRA; ++r)
           dev::sincos_cycles_mufu(dev::frac_rn(dev::frac_product_plus(qz, z[r], base[r])), &ei[r], &er[r]);
+        u64 er2[kP], ei2[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          er2[p] = dev::pack2(er[2 * p], er[2 * p + 1]);
+          ei2[p] = dev::pack2(ei[2 * p], ei[2 * p + 1]);
+        }
         const int je = min(cnt, jb + kReseed);
 #pragma unroll 2
         for (int j = jb; j < je; ++j) {
           const float4 q = sv4[j];  // s_z, S_z, gF.re, gF.im
+          const u64 qy2 = dev::pack2(q.y, q.y), qz2 = dev::pack2(q.z, q.z), qw2 = dev::pack2(q.w, q.w);
 #pragma unroll
-          for (int r = 0; r < kAdjRA; ++r) {
-            const float v = fmaf(q.z, ei[r], q.w * er[r]);  // Im(gF e)
-            sv[r] += v;
-            szv[r] = fmaf(q.y, v, szv[r]);
-            const float nr = fmaf(er[r], wr[r], -ei[r] * wi[r]);
-            ei[r] = fmaf(er[r], wi[r], ei[r] * wr[r]);
-            er[r] = nr;
+          for (int p = 0; p < kP; ++p) {
+            const u64 v = dev::fma2(qz2, ei2[p], dev::fma2(qw2, er2[p], zero2));  // Im(gF e)
+            sv2[p] = dev::fma2(v, one2, sv2[p]);
+            szv2[p] = dev::fma2(qy2, v, szv2[p]);
+            const u64 nr = dev::fma2(er2[p], wr2[p], dev::fma2(ei2[p], nwi2[p], zero2));
+            ei2[p] = dev::fma2(er2[p], wi2[p], dev::fma2(ei2[p], wr2[p], zero2));
+            er2[p] = nr;
           }
         }
+      }
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        dev::unpack2(sv2[p], sv[2 * p], sv[2 * p + 1]);
+        dev::unpack2(szv2[p], szv[2 * p], szv[2 * p + 1]);
       }
     }
     const float Sx = a.H[0] + sx, Sy = a.H[1] + sy;

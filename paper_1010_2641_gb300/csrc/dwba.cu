@@ -104,20 +104,6 @@ __global__ void k_dwba_ztable(const float4* __restrict__ atom4, const float4* __
   ztab[i] = make_float4(w1 * c1, w1 * s1, w2 * c2, w2 * s2);
 }
 
-// Two FP32 values in one 64-bit register pair, for the packed f32x2 FMA.
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-// d = a * b + d on both halves (one instruction for two FP32 FMAs)
-__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-
 // Tile sums of the four real products of E_j = w_j e^{2 pi i (s_h x'_j + s_k y'_j + c_j)}
 // with each Z of the thread's rows: [P, Q, R, T] of Z1, then of Z2.  The
 // products that share a factor of E run as packed pairs: (P, R) += Er (Zr, Zi)
@@ -148,24 +134,24 @@ __device__ __forceinline__ void dwba_tile_products(const float4* zs, const float
     }
     float er, ei;  // E / w (the table carries w)
     dev::sincos_cycles_mufu(f, &ei, &er);
-    const unsigned long long er2 = pack2(er, er), ei2 = pack2(ei, ei);
+    const unsigned long long er2 = dev::pack2(er, er), ei2 = dev::pack2(ei, ei);
     const float4* zr = zs + j * kAfBlock + af_l0;
 #pragma unroll
     for (int r = 0; r < kDwbaR; ++r) {
       const float4 z = zr[r];  // Z1 (re, im), Z2 (re, im)
-      const unsigned long long z1 = pack2(z.x, z.y), z2 = pack2(z.z, z.w);
-      ffma2(pk[r][0], er2, z1);
-      ffma2(pk[r][1], ei2, z1);
-      ffma2(pk[r][2], er2, z2);
-      ffma2(pk[r][3], ei2, z2);
+      const unsigned long long z1 = dev::pack2(z.x, z.y), z2 = dev::pack2(z.z, z.w);
+      dev::ffma2(pk[r][0], er2, z1);
+      dev::ffma2(pk[r][1], ei2, z1);
+      dev::ffma2(pk[r][2], er2, z2);
+      dev::ffma2(pk[r][3], ei2, z2);
     }
   }
 #pragma unroll
   for (int r = 0; r < kDwbaR; ++r) {
-    unpack2(pk[r][0], acc[r][0], acc[r][2]);  // P1, R1
-    unpack2(pk[r][1], acc[r][3], acc[r][1]);  // T1, Q1
-    unpack2(pk[r][2], acc[r][4], acc[r][6]);  // P2, R2
-    unpack2(pk[r][3], acc[r][7], acc[r][5]);  // T2, Q2
+    dev::unpack2(pk[r][0], acc[r][0], acc[r][2]);  // P1, R1
+    dev::unpack2(pk[r][1], acc[r][3], acc[r][1]);  // T1, Q1
+    dev::unpack2(pk[r][2], acc[r][4], acc[r][6]);  // P2, R2
+    dev::unpack2(pk[r][3], acc[r][7], acc[r][5]);  // T2, Q2
   }
 }
 
