@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
 // exponential is re-seeded from the exactly reduced phase, which bounds the
 // rounding drift of the recurrence to ~64 products (~1e-5 relative, against
 // the 1e-3 tolerance of the gradients).  Per tile: FP32 line sums
-// sum v and sum S_z v, folded into the FP64 outer sums as S_x sum v,
-// S_y sum v, sum S_z v.
+// sum v and sum S_z v, folded into double-float outer sums (FP32 pairs on
+// the FMA pipe) as S_x sum v, S_y sum v, sum S_z v.
 struct AdjLineArgs {
   const float4* atom4;
   const AdjBlock* blocks;
@@ -299,9 +299,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     wr[r] = cs;
     wi[r] = sn;
   }
-  double gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
-#pragma unroll
-  for (int r = 0; r < kAdjRA; ++r) gx[r] = gy[r] = gz[r] = 0.0;
+  // outer sums over the lines: double-float on the FP32 pipe
+  dev::DFloatSum gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
 
   if (tid == 0) {
     dev::mbar_init(&sh_bar[0], 1);
@@ -390,9 +389,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     const float Sx = a.H[0] + sx, Sy = a.H[1] + sy;
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) {
-      gx[r] += (double)Sx * (double)sv[r];
-      gy[r] += (double)Sy * (double)sv[r];
-      gz[r] += (double)szv[r];
+      gx[r].add_product(Sx, sv[r]);
+      gy[r].add_product(Sy, sv[r]);
+      gz[r].add(szv[r]);
     }
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -412,9 +411,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     const int i = r * kAdjThreads + tid;
     if (i < blk.count) {
       const int64_t slot = blk.begin + i;
-      out[3 * slot] = (float)gx[r];
-      out[3 * slot + 1] = (float)gy[r];
-      out[3 * slot + 2] = (float)gz[r];
+      out[3 * slot] = gx[r].value();
+      out[3 * slot + 1] = gy[r].value();
+      out[3 * slot + 2] = gz[r].value();
     }
   }
 }

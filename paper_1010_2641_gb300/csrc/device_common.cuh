@@ -97,6 +97,32 @@ __device__ __forceinline__ float frac_of_product2(float a, float alo, float b) {
   return (p - rintf(p)) + fmaf(alo, b, fmaf(a, b, -p));
 }
 
+// Running sum as an unevaluated FP32 pair hi + lo (about 2^-44 relative to
+// the partial sums, against FP64's 2^-53) on the FP32 pipe, for the places
+// where an FP64 accumulator would issue at GB300's small FP64 rate.  Each
+// addition is Knuth's branch-free TwoSum: the exact rounding error of
+// hi + x gathers in lo.  A product enters with its own exact rounding error
+// (FMA), so hi + lo equals the FP64 sum of the exact products up to the
+// rounding of lo.  The _rn intrinsics keep the compiler from contracting or
+// reordering the error terms.
+struct DFloatSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void add_product(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
+};
+
 // sin and cos of 2*pi*f for |f| <= 1/2 (cycles) on the MUFU pipe
 // (sin.approx/cos.approx: absolute error below 1e-6 on [-pi, pi]).
 __device__ __forceinline__ void sincos_cycles_mufu(float f, float* s, float* c) {
@@ -151,6 +177,20 @@ __device__ __forceinline__ float2 shift_phase(double s0, double s1, double s2, c
   const float f = (float)(ph - rint(ph));
   float sn, cs;
   sincospif(2.0f * f, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// The same phase without FP64 arithmetic (GB300 issues FP64 at a small
+// fraction of the FP32 rate): offsets as double-floats s_hi + s_lo, t_d
+// integers below 2^24 in FP32.  Each s_d t_d has its fractional part taken
+// with the product's rounding error restored (error ~2^-24 per term, as the
+// FP64 form's final rounding to FP32).
+__device__ __forceinline__ float2 shift_phase2(const float (&s_hi)[3], const float (&s_lo)[3], const float (&t)[3]) {
+  float f = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) f += frac_of_product2(s_hi[d], s_lo[d], t[d]);
+  float sn, cs;
+  sincospif(2.0f * frac_rn(f), &sn, &cs);
   return make_float2(cs, sn);
 }
 

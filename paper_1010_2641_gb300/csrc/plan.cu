@@ -307,7 +307,6 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.ftab64);
   release(d.sep_axis_s);
   release(d.sep_axis_lo);
-  release(d.sep_axis64);
   release(d.sep_virt);
   release(d.batch_inst);
   release(d.batch_items);

@@ -131,7 +131,6 @@ struct DeviceBuffers {
   double* ftab64 = nullptr;         // the same in FP64 (re, im) for the FP64 kernel
   float* sep_axis_s = nullptr;      // separable grid axes, s = axis - H (virtual for GID)
   float* sep_axis_lo = nullptr;     // their FP32 rounding errors
-  double* sep_axis64 = nullptr;     // separable grid axes, full S
   float2* sep_virt = nullptr;       // GID: map over the virtual (h, k, 4 beams x alpha_f) grid
   // batches
   BatchInst* batch_inst = nullptr;

@@ -144,9 +144,5 @@ cudaError_t sep_prepare_kernel();
 cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);
 cudaError_t sep_pair_prepare_kernel();
 bool sep_pair_enabled();
-// The CTA-pair form (sep_pair.cu): n_nt N tiles, n_chunks atom chunks.
-cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);
-cudaError_t sep_pair_prepare_kernel();
-bool sep_pair_enabled();
 
 }  // namespace scatter

@@ -72,17 +72,22 @@ struct SepTabArgs {
 __global__ void k_sep_tab_a(const SepTabArgs t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = t.n_mt * t.n_steps * 4 * kSepM;
+  // total is a multiple of 512: whole warps leave here, the shuffles below
+  // always see all 32 lanes
   if (i >= total) return;
   const int r = (int)(i % 8), mg = (int)((i / 8) % 16), kb = (int)((i / 128) % 4);
   const int64_t ks = (i / 512) % t.n_steps, mt = i / (512 * t.n_steps);
   const int64_t m = mt * kSepM + mg * 8 + r;
   const int64_t a = m >> 1;
   const int ri = (int)(m & 1);
-  float v[8];
+  // lanes 2a' and 2a'+1 (rows Re and Im of the same h) share X(h, atom):
+  // each evaluates two of the block's four atoms and takes the other two
+  // from its neighbour
+  float sq[2], cq[2];
   const float sa = a < t.n0 ? t.axis_s[a] : 0.f, sal = a < t.n0 ? t.axis_lo[a] : 0.f;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t slot = ks * kSepStep + kb * 4 + q;
+  for (int u = 0; u < 2; ++u) {
+    const int64_t slot = ks * kSepStep + kb * 4 + 2 * ri + u;
     float sn = 0.f, cs = 0.f;
     if (a < t.n0) {
       sincospif(2.0f * (dev::frac_of_product2(sa, sal, t.atom4[slot].x) + sa * t.atom_lo[slot].x), &sn, &cs);
@@ -90,6 +95,16 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
       sn *= w;
       cs *= w;
     }
+    sq[u] = sn;
+    cq[u] = cs;
+  }
+  float v[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int u = q & 1;
+    const float ps = __shfl_xor_sync(0xffffffffu, sq[u], 1), pc = __shfl_xor_sync(0xffffffffu, cq[u], 1);
+    const bool own = (q >> 1) == ri;
+    const float sn = own ? sq[u] : ps, cs = own ? cq[u] : pc;
     // row 2a: (Xr, -Xi); row 2a+1: (Xi, Xr)
     v[2 * q] = ri ? sn : cs;
     v[2 * q + 1] = ri ? cs : -sn;
@@ -443,34 +458,97 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
 
 // Sum over the chunks in order of f_s(|S|) x T_chunk (Eq. 2: each chunk holds
 // one species s), translation phase, outputs.
-__global__ void k_sep_reduce(const float* __restrict__ partial, int64_t chunk_floats, int64_t n_cb,
-                             const Segment* __restrict__ chunks, int n_chunks,
-                             const float* __restrict__ coef, const float2* __restrict__ ftab, float inv4a2, int64_t n_s,
-                             const double* __restrict__ axis64, int64_t n0, int64_t n1, int64_t n2, double H0,
-                             double H1, double H2, const double* __restrict__ shift, float2* out_amp, float* out_int) {
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= n_s) return;
-  const int64_t i2 = m % n2, line = m / n2, i1 = line % n1, i0 = line / n1;
-  const double S0 = axis64[i0], S1 = axis64[n0 + i1], S2 = axis64[n0 + n1 + i2];
-  const float s2 = (float)(S0 * S0 + S1 * S1 + S2 * S2) * inv4a2;
-  float2 v = make_float2(0.f, 0.f), F = make_float2(0.f, 0.f);
-  int cur = -1;
-  for (int c = 0; c < n_chunks; ++c) {
-    const int sp = chunks[c].species;
-    if (sp != cur) {
-      F = ftab ? ftab[(int64_t)sp * n_s + m] : dev::form_factor(coef + kNCoef * sp, s2);
-      cur = sp;
-    }
-    const float* pc = partial + (int64_t)c * chunk_floats;
-    const int64_t col = m - i0 * n1 * n2;  // the point's (b, c) column
-    const float re = pc[sep_part_off(2 * i0, col, n_cb)], im = pc[sep_part_off(2 * i0 + 1, col, n_cb)];
-    v.x += F.x * re - F.y * im;
-    v.y += F.x * im + F.y * re;
+// Sum of the chunks' partials with f_s(|S|) per chunk's species, the
+// centring phase and |A|^2.  One CTA per 32 x 32 block of the blocked
+// partials (16 h values x 32 (k, l) columns, 512 points): each chunk's block
+// is 4 KB contiguous and is read as one float4 per thread, thread t holding
+// D row t % 32 (Re of h row (t % 32) / 2 for even t % 32, Im for odd) of the
+// columns 4 (t / 32) .. +3.  One exchange between the two lanes of a row
+// pair gives lane 2i columns 4q, 4q+1 and lane 2i+1 columns 4q+2, 4q+3 (two
+// points each).  The sum over chunks runs in chunk order, eight chunks' loads
+// in flight.
+__global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ partial, int64_t chunk_floats,
+                                                    int64_t n_cb, const Segment* __restrict__ chunks, int n_chunks,
+                                                    const float* __restrict__ coef, const float2* __restrict__ ftab,
+                                                    float inv4a2, const float* __restrict__ axis_s,
+                                                    const float* __restrict__ axis_lo, int64_t n0, int64_t n1,
+                                                    int64_t n2, float3 H, const double* __restrict__ shift,
+                                                    float2* out_amp, float* out_int) {
+  // the centring shift of the call (integers), once per block
+  __shared__ float sh_t[3];
+  __shared__ int sh_shifted;
+  if (threadIdx.x == 0) {
+    sh_t[0] = (float)shift[0];
+    sh_t[1] = (float)shift[1];
+    sh_t[2] = (float)shift[2];
+    sh_shifted = shift[0] != 0.0 || shift[1] != 0.0 || shift[2] != 0.0;
   }
-  if (shift[0] != 0.0 || shift[1] != 0.0 || shift[2] != 0.0)
-    v = dev::cmul(dev::shift_phase(S0 - H0, S1 - H1, S2 - H2, shift), v);
-  if (out_amp) out_amp[m] = v;
-  if (out_int) out_int[m] = v.x * v.x + v.y * v.y;
+  __syncthreads();
+  const int t = threadIdx.x, lane = t & 31, odd = lane & 1;
+  const int64_t bm = blockIdx.y, bc = blockIdx.x;
+  const int64_t ncols = n1 * n2, n_s = n0 * ncols;
+  const int64_t i0 = bm * 16 + (lane >> 1);
+  const int64_t col0 = bc * 32 + (t >> 5) * 4 + odd * 2;  // the thread's two columns
+  // per point: double-float offsets s, |S|^2 / (4 a^2) in FP32 (S = H + s)
+  float s_hi[2][3], s_lo[2][3], s2[2];
+  bool ok[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int64_t col = col0 + u;
+    ok[u] = i0 < n0 && col < ncols;
+    const int64_t ia[3] = {ok[u] ? i0 : 0, n0 + (ok[u] ? col / n2 : 0), n0 + n1 + (ok[u] ? col % n2 : 0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      s_hi[u][d] = axis_s[ia[d]];
+      s_lo[u][d] = axis_lo[ia[d]];
+    }
+    const float S0 = H.x + (s_hi[u][0] + s_lo[u][0]), S1 = H.y + (s_hi[u][1] + s_lo[u][1]),
+                S2 = H.z + (s_hi[u][2] + s_lo[u][2]);
+    s2[u] = (S0 * S0 + S1 * S1 + S2 * S2) * inv4a2;
+  }
+  const int64_t m0 = i0 * ncols + col0;
+  const float* blk = partial + (bm * n_cb + bc) * 1024 + 4 * t;
+  float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, F[2] = {v[0], v[1]};
+  int cur = -1;
+  constexpr int kU = 8;
+  for (int c0 = 0; c0 < n_chunks; c0 += kU) {
+    float4 x[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      x[u] = c0 + u < n_chunks ? __ldcs(reinterpret_cast<const float4*>(blk + (int64_t)(c0 + u) * chunk_floats))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (c0 + u >= n_chunks) break;  // uniform over the block
+      // even lane: Re of columns 4q..4q+3, needs Im of 4q, 4q+1; odd lane:
+      // Im, needs Re of 4q+2, 4q+3
+      const float sx = odd ? x[u].x : x[u].z, sy = odd ? x[u].y : x[u].w;
+      const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+      const float re[2] = {odd ? rx : x[u].x, odd ? ry : x[u].y};
+      const float im[2] = {odd ? x[u].z : rx, odd ? x[u].w : ry};
+      const int sp = chunks[c0 + u].species;
+      if (sp != cur) {
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+          F[w] = ftab ? (ok[w] ? ftab[(int64_t)sp * n_s + m0 + w] : make_float2(0.f, 0.f))
+                      : dev::form_factor(coef + kNCoef * sp, s2[w]);
+        cur = sp;
+      }
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        v[w].x += F[w].x * re[w] - F[w].y * im[w];
+        v[w].y += F[w].x * im[w] + F[w].y * re[w];
+      }
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    if (!ok[w]) continue;
+    float2 a = v[w];
+    if (sh_shifted) a = dev::cmul(dev::shift_phase2(s_hi[w], s_lo[w], sh_t), a);
+    if (out_amp) out_amp[m0 + w] = a;
+    if (out_int) out_int[m0 + w] = a.x * a.x + a.y * a.y;
+  }
 }
 
 // -------------------------------------------------------------------------
@@ -541,12 +619,10 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   } else {
     ax64[2] = p->axis_host[2];
   }
-  std::vector<double> all64;
   std::vector<float> alls, alls_lo;
   for (int d = 0; d < 3; ++d) {
     p->sep_n[d] = (int64_t)ax64[d].size();
     for (double v : ax64[d]) {
-      all64.push_back(v);
       const double sv = v - p->inst[0].H[d];
       alls.push_back((float)sv);
       alls_lo.push_back((float)(sv - (double)(float)sv));
@@ -608,10 +684,8 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   cudaMemcpy(p->d.sep_chunks, chunks.data(), chunk_bytes, cudaMemcpyHostToDevice);
   if ((e = cudaMalloc(&p->d.sep_axis_s, alls.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
   if ((e = cudaMalloc(&p->d.sep_axis_lo, alls_lo.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "axes");
-  if ((e = cudaMalloc(&p->d.sep_axis64, all64.size() * sizeof(double))) != cudaSuccess) return cuda_status(e, "axes");
   cudaMemcpy(p->d.sep_axis_s, alls.data(), alls.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d.sep_axis_lo, alls_lo.data(), alls_lo.size() * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d.sep_axis64, all64.data(), all64.size() * sizeof(double), cudaMemcpyHostToDevice);
   size_t virt_bytes = 0;
   if (gid) {
     virt_bytes = (size_t)p->sep_ns * sizeof(float2);
@@ -670,13 +744,14 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   if (le != cudaSuccess) return cuda_status(le, "separable kernel launch");
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
-  k_sep_reduce<<<(unsigned)((p->sep_ns + 255) / 256), 256, 0, st>>>(
-      p->d.sep_partial, sep_part_floats(p->sep_mt, p->sep_n[1] * p->sep_n[2]),
-      (p->sep_n[1] * p->sep_n[2] + 31) / 32, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
-      (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
-      p->sep_ns, p->d.sep_axis64, p->sep_n[0], p->sep_n[1], p->sep_n[2],
-      p->inst[0].H[0], p->inst[0].H[1], p->inst[0].H[2], p->d.inst_shift, gid ? p->d.sep_virt : amp_out,
-      gid ? nullptr : int_out);
+  const int64_t n_cb = (p->sep_n[1] * p->sep_n[2] + 31) / 32;
+  const dim3 rgrid((unsigned)n_cb, (unsigned)((2 * p->sep_n[0] + 31) / 32));
+  k_sep_reduce<<<rgrid, 256, 0, st>>>(
+      p->d.sep_partial, sep_part_floats(p->sep_mt, p->sep_n[1] * p->sep_n[2]), n_cb, p->d.sep_chunks, n_chunks,
+      p->d.coef, p->d.ftab, (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
+      p->d.sep_axis_s, p->d.sep_axis_lo, p->sep_n[0], p->sep_n[1], p->sep_n[2],
+      make_float3((float)p->inst[0].H[0], (float)p->inst[0].H[1], (float)p->inst[0].H[2]), p->d.inst_shift,
+      gid ? p->d.sep_virt : amp_out, gid ? nullptr : int_out);
   p->last_launches += 1;
   if (gid) {
     scatter_status s2 = launch_gid_combine(p, amp_out, int_out, st);

@@ -5,7 +5,7 @@ Every value in the files this script writes comes from the FP64 CPU oracle
 ``paper_1010_2641_gb300.workloads``; nothing is taken from the GPU library.
 Run it on the host (it takes hours of CPU time on a few cores):
 
-    python tests/golden/make_golden.py [--only island|cube|batch] [--threads N]
+    python tests/golden/make_golden.py [--only island|cube|batch|sphere] [--threads N]
 
 Files (numpy ``.npz``; each holds a ``meta`` JSON string naming this script,
 the workload, its seeds and the oracle calls):
@@ -20,6 +20,10 @@ the workload, its seeds and the oracle calls):
                            the perturbed copy, the misfit L, the analytic
                            gradient and central differences for 50 seeded
                            atoms
+  sphere_subgrid.npz       the 134,009-atom strained fcc sphere on the 1/16
+                           sub-grid of its 256 x 256 x 64 map around (004):
+                           every 4th h and every 4th k, all l (262,144
+                           points), A of Eq. 2
   ewald_batch_sample.npz   the 64-crystal Ewald-slice batch: full maps of the
                            instances with N_b M_b <= 2e8 and a seeded 1 %
                            (at least 1024 points) of every other instance's
@@ -51,6 +55,8 @@ ISLAND_STRIDE = 8
 # strained cube: 50 seeded atoms for the gradient checks
 CUBE_SEL_SEED, CUBE_N_SEL, CUBE_FD_H = 4002, 50, 1e-5
 CUBE_N, CUBE_STEP = 128, 0.005
+# strained sphere: every 4th h and k of the 256 x 256 x 64 map, step 0.002
+SPHERE_GRID, SPHERE_STEP, SPHERE_STRIDE = (256, 256, 64), 0.002, 4
 # Ewald batch: full maps up to this many pairs, else a 1 % sample
 BATCH_FULL_PAIRS, BATCH_FRACTION, BATCH_MIN_POINTS, BATCH_SAMPLE_SEED = 2e8, 0.01, 1024, 3100
 
@@ -63,6 +69,17 @@ def island_subgrid_axes():
 def cube_axes():
     return [W.linspace_axis(0.0, CUBE_N, step=CUBE_STEP), W.linspace_axis(0.0, CUBE_N, step=CUBE_STEP),
             W.linspace_axis(4.0, CUBE_N, step=CUBE_STEP)]
+
+
+def sphere_axes():
+    n0, n1, n2 = SPHERE_GRID
+    return [W.linspace_axis(0.0, n0, step=SPHERE_STEP), W.linspace_axis(0.0, n1, step=SPHERE_STEP),
+            W.linspace_axis(4.0, n2, step=SPHERE_STEP)]
+
+
+def sphere_subgrid_axes():
+    h, k, l = sphere_axes()
+    return h[::SPHERE_STRIDE], k[::SPHERE_STRIDE], l
 
 
 def cube_selected_atoms(n_atoms: int) -> np.ndarray:
@@ -124,6 +141,20 @@ def make_cube(out: pathlib.Path) -> None:
     np.savez(out, meta=meta, A=A.astype(np.complex64), I_obs=I_obs, loss=np.float64(L), atoms=sel, grad=g, fd=fd)
 
 
+def make_sphere(out: pathlib.Path) -> None:
+    c = W.fcc_sphere()
+    h, k, l = sphere_subgrid_axes()
+    pts = W.grid_points([h, k, l])
+    t0 = time.time()
+    A = oracle.amplitude(c.xyz, pts, c.coef, A_LAT, species=c.species)
+    meta = _meta(workload="fcc_sphere() (radius 20 cells, 2 species, seed 2000) on the 256 x 256 x 64 grid "
+                          "around (0,0,4), step 0.002, every 4th h and k, all l",
+                 seeds={"crystal": 2000}, oracle="oracle.amplitude", n_atoms=len(c.xyz),
+                 shape=[len(h), len(k), len(l)], stride=SPHERE_STRIDE, seconds=round(time.time() - t0, 1),
+                 threads=oracle.num_threads())
+    np.savez(out, meta=meta, A=A.astype(np.complex64))
+
+
 def make_batch(out: pathlib.Path) -> None:
     xyz, sp, coef, S, ao, so = W.ewald_batch()
     idx, off, full = batch_sample(ao, so)
@@ -140,7 +171,7 @@ def make_batch(out: pathlib.Path) -> None:
 
 
 JOBS = {"batch": ("ewald_batch_sample.npz", make_batch), "island": ("island_gid_subgrid.npz", make_island),
-        "cube": ("strained_cube_128.npz", make_cube)}
+        "cube": ("strained_cube_128.npz", make_cube), "sphere": ("sphere_subgrid.npz", make_sphere)}
 
 
 def main() -> None:
