@@ -260,6 +260,33 @@ scatter_status scatter_amplitude(scatter_plan_t plan, const double* xyz,
                                  const float* occ, void* A_out, void* stream);
 
 /*
+ * scatter_amplitude_host — scatter_amplitude with host buffers, the shape of
+ * the paper's own call (Section 3: positions in, amplitudes out, both
+ * host arrays).
+ *
+ *  xyz    host float64 [n_atoms][3], lattice units, caller's atom order.
+ *  occ    host float32 [n_atoms] occupancies, or NULL (all 1).
+ *  A_out  host complex64 [n_s], written in full once the stream's work
+ *         completes (synchronise `stream`, or scatter_check, before reading).
+ *  stream CUDA stream or NULL.
+ *
+ * The plan copies the inputs into device buffers of its own (allocated on
+ * the first host call and kept until scatter_plan_destroy: 28 n_atoms + 8 n_s
+ * bytes, plus a second stream and five events), runs the plan's forward on
+ * them and copies the map back.  On a SEPARABLE plan of a GRID the final
+ * reduction runs in four ranges of map rows and each range's copy to the
+ * host starts on the plan's second stream as soon as that range is reduced,
+ * overlapping the rest of the reduction; `stream` waits for the last copy.
+ * Pinned host memory gives asynchronous copies; pageable memory is accepted
+ * and then copied synchronously by the driver.  Errors: INVALID_ARG for a
+ * NULL or device pointer (a NULL xyz or A_out is allowed only when n_atoms
+ * or n_s is 0); OOM when the staging buffers cannot be allocated; the
+ * forward's errors otherwise.  Calls on one plan must not overlap.
+ */
+scatter_status scatter_amplitude_host(scatter_plan_t plan, const double* xyz,
+                                      const float* occ, void* A_out, void* stream);
+
+/*
  * scatter_intensity — I(S) = |A(S)|^2 (the quantity of the paper's maps,
  * Section 2.3).  Same inputs as scatter_amplitude; I_out is device float32
  * [n_s].  A is formed in the plan's workspace.

@@ -188,6 +188,33 @@ class Plan:
                 "scatter_amplitude")
         return out
 
+    def amplitude_host(self, xyz, occ=None, out=None, stream=None) -> torch.Tensor:
+        """A(S) from host positions into a host map (scatter_amplitude_host).
+
+        `xyz` is a CPU float64 [N, 3] tensor or array (pinned for an
+        asynchronous call), `out` a CPU complex64 [n_s] tensor (allocated
+        pinned if not given).  The call enqueues on `stream`; synchronise it
+        before reading `out`."""
+        x = torch.as_tensor(xyz, dtype=torch.float64)
+        if x.device.type != "cpu":
+            raise ValueError("amplitude_host takes host positions; use amplitude for device tensors")
+        x = x.contiguous()
+        if x.shape != (self.n_atoms, 3):
+            raise ValueError(f"xyz must be [{self.n_atoms}, 3]")
+        o = None
+        if occ is not None:
+            o = torch.as_tensor(occ, dtype=torch.float32).contiguous()
+            if o.device.type != "cpu" or o.shape != (self.n_atoms,):
+                raise ValueError(f"occ must be a host [{self.n_atoms}] tensor")
+        if out is None:
+            out = torch.empty(self.n_s, dtype=torch.complex64).pin_memory()
+        elif out.device.type != "cpu" or out.dtype != torch.complex64 or out.numel() != self.n_s \
+                or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous host complex64 [{self.n_s}] tensor")
+        B.check(B.lib().scatter_amplitude_host(self._h, _ptr(x), _ptr(o), _ptr(out), _stream(stream)),
+                "scatter_amplitude_host")
+        return out
+
     def intensity(self, xyz, occ=None, out=None, stream=None) -> torch.Tensor:
         xyz, occ = self._xyz(xyz), self._occ(occ)
         if out is None:

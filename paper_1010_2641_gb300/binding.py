@@ -97,6 +97,7 @@ _PROTOTYPES = {
     "scatter_plan": (c_int32, [ctypes.POINTER(scatter_problem), ctypes.POINTER(scatter_options),
                                ctypes.POINTER(c_void_p)]),
     "scatter_amplitude": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scatter_amplitude_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "scatter_intensity": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "scatter_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p]),

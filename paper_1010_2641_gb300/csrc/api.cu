@@ -130,6 +130,86 @@ extern "C" scatter_status scatter_amplitude(scatter_plan_t p, const double* xyz,
   return forward(p, xyz, occ, static_cast<float2*>(A_out), nullptr, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+
+// A host pointer (pinned or pageable); NULL only if allowed.
+scatter_status check_host_ptr(const void* ptr, const char* name, bool allow_null) {
+  if (!ptr) {
+    if (allow_null) return SCATTER_OK;
+    return fail(SCATTER_ERR_INVALID_ARG, "%s is NULL", name);
+  }
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return SCATTER_OK;  // memory CUDA does not know: pageable host memory
+  }
+  if (at.type == cudaMemoryTypeDevice) return fail(SCATTER_ERR_INVALID_ARG, "%s must be host memory", name);
+  return SCATTER_OK;
+}
+
+// Device copies of a host call's buffers, and the copy-out stream and events.
+scatter_status ensure_host_staging(scatter_plan_t p, bool with_occ) {
+  cudaError_t e;
+  auto grow = [&](void** buf, size_t bytes, const char* what) -> scatter_status {
+    if (*buf || bytes == 0) return SCATTER_OK;
+    if ((e = cudaMalloc(buf, bytes)) != cudaSuccess) return cuda_status(e, what);
+    p->base_bytes += (int64_t)bytes;
+    return SCATTER_OK;
+  };
+  scatter_status s;
+  if ((s = grow((void**)&p->d.host_xyz, (size_t)p->n_atoms * 3 * sizeof(double), "host-call positions"))) return s;
+  if (with_occ && (s = grow((void**)&p->d.host_occ, (size_t)p->n_atoms * sizeof(float), "host-call occupancies")))
+    return s;
+  if ((s = grow((void**)&p->d.host_amp, (size_t)p->n_s * sizeof(float2), "host-call amplitudes"))) return s;
+  if (!p->copy_stream && (e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_status(e, "copy stream");
+  for (cudaEvent_t& ev : p->copy_ev)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_status(e, "copy events");
+  return SCATTER_OK;
+}
+
+}  // namespace
+
+extern "C" scatter_status scatter_amplitude_host(scatter_plan_t p, const double* xyz, const float* occ, void* A_out,
+                                                 void* stream) {
+  if (!p) return fail(SCATTER_ERR_INVALID_ARG, "plan is NULL");
+  scatter_status st = check_host_ptr(xyz, "xyz", p->n_atoms == 0);
+  if (st == SCATTER_OK) st = check_host_ptr(occ, "occ", true);
+  if (st == SCATTER_OK) st = check_host_ptr(A_out, "A_out", p->n_s == 0);
+  if (st != SCATTER_OK) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SCATTER_ERR_CUDA, "cannot select the plan's device");
+  if ((st = ensure_host_staging(p, occ != nullptr)) != SCATTER_OK) return st;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (p->n_atoms > 0 &&
+      (e = cudaMemcpyAsync(p->d.host_xyz, xyz, (size_t)p->n_atoms * 3 * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return cuda_status(e, "positions to the device");
+  if (occ && p->n_atoms > 0 &&
+      (e = cudaMemcpyAsync(p->d.host_occ, occ, (size_t)p->n_atoms * sizeof(float), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return cuda_status(e, "occupancies to the device");
+  const float* docc = occ ? p->d.host_occ : nullptr;
+  if (p->n_s == 0) return SCATTER_OK;
+  // a separable grid copies its map out in row ranges while the rest is
+  // reduced (inside launch_separable); other plans copy it after the call
+  const bool pieces = p->path == SCATTER_PATH_SEPARABLE && p->s_kind == SCATTER_S_GRID && p->batch == 1;
+  if (pieces) {
+    p->host_out = A_out;
+    p->last_launches = 0;
+    st = enqueue_single(p, p->d.host_xyz, docc, p->d.host_amp, nullptr, s);
+    p->host_out = nullptr;
+    return st;
+  }
+  if ((st = forward(p, p->d.host_xyz, docc, p->d.host_amp, nullptr, s)) != SCATTER_OK) return st;
+  if ((e = cudaMemcpyAsync(A_out, p->d.host_amp, (size_t)p->n_s * sizeof(float2), cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return cuda_status(e, "amplitudes to the host");
+  return SCATTER_OK;
+}
+
 extern "C" scatter_status scatter_intensity(scatter_plan_t p, const double* xyz, const float* occ, float* I_out,
                                             void* stream) {
   scatter_status st = check_inputs(p, xyz, occ);

@@ -327,6 +327,12 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   release(d.adj_kchunks);
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);
   if (p->ev_end) cudaEventDestroy(p->ev_end);
+  release(d.host_xyz);
+  release(d.host_occ);
+  release(d.host_amp);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (cudaEvent_t& e : p->copy_ev)
+    if (e) cudaEventDestroy(e);
   if (prev >= 0) cudaSetDevice(prev);
   delete p;
 }

@@ -81,6 +81,10 @@ struct Tiling {
   int atom_k = 0;     // > 0: atom-parallel form, atoms per thread (atompar.cu)
 };
 
+// row ranges of a separable map reduced and copied out one after another by
+// scatter_amplitude_host
+constexpr int kHostPieces = 4;
+
 struct DeviceBuffers {
   int32_t* slot_src = nullptr;      // [n_slots]
   int32_t* slot_inst = nullptr;     // [n_slots]
@@ -148,6 +152,10 @@ struct DeviceBuffers {
   float4* adj_rec = nullptr;        // point records (0, s_b, s_c, 0), 16 per step
   Segment* adj_ntiles = nullptr;    // 256-slot atom tiles of one species
   Segment* adj_kchunks = nullptr;   // point-step chunks (split over K)
+  // scatter_amplitude_host: device copies of the caller's host buffers
+  double* host_xyz = nullptr;       // [n_atoms][3]
+  float* host_occ = nullptr;        // [n_atoms]
+  float2* host_amp = nullptr;       // [n_s]
 };
 
 }  // namespace scatter
@@ -210,4 +218,10 @@ struct scatter_plan_s {
   int64_t adj_sep_ksteps = 0, adj_sep_mt = 0;
   int32_t adj_sep_ntiles = 0, adj_sep_chunks = 0;
   float adj_sep_smax[2] = {0.f, 0.f};
+  // scatter_amplitude_host on a separable grid: the reduction runs in
+  // kHostPieces row ranges and each range's copy to the host (destination
+  // host_out) starts on copy_stream as soon as the range is reduced
+  void* host_out = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[scatter::kHostPieces + 1] = {};
 };

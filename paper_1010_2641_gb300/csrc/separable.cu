@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ pa
                                                     float inv4a2, const float* __restrict__ axis_s,
                                                     const float* __restrict__ axis_lo, int64_t n0, int64_t n1,
                                                     int64_t n2, float3 H, const double* __restrict__ shift,
-                                                    float2* out_amp, float* out_int) {
+                                                    int64_t bm_base, float2* out_amp, float* out_int) {
   // the centring shift of the call (integers), once per block
   __shared__ float sh_t[3];
   __shared__ int sh_shifted;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ pa
   }
   __syncthreads();
   const int t = threadIdx.x, lane = t & 31, odd = lane & 1;
-  const int64_t bm = blockIdx.y, bc = blockIdx.x;
+  const int64_t bm = bm_base + blockIdx.y, bc = blockIdx.x;
   const int64_t ncols = n1 * n2, n_s = n0 * ncols;
   const int64_t i0 = bm * 16 + (lane >> 1);
   const int64_t col0 = bc * 32 + (t >> 5) * 4 + odd * 2;  // the thread's two columns
@@ -745,14 +745,37 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   p->last_launches += 1;
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   const int64_t n_cb = (p->sep_n[1] * p->sep_n[2] + 31) / 32;
-  const dim3 rgrid((unsigned)n_cb, (unsigned)((2 * p->sep_n[0] + 31) / 32));
-  k_sep_reduce<<<rgrid, 256, 0, st>>>(
-      p->d.sep_partial, sep_part_floats(p->sep_mt, p->sep_n[1] * p->sep_n[2]), n_cb, p->d.sep_chunks, n_chunks,
-      p->d.coef, p->d.ftab, (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)),
-      p->d.sep_axis_s, p->d.sep_axis_lo, p->sep_n[0], p->sep_n[1], p->sep_n[2],
-      make_float3((float)p->inst[0].H[0], (float)p->inst[0].H[1], (float)p->inst[0].H[2]), p->d.inst_shift,
-      gid ? p->d.sep_virt : amp_out, gid ? nullptr : int_out);
-  p->last_launches += 1;
+  const int64_t n_bm = (2 * p->sep_n[0] + 31) / 32;  // 32-row blocks holding map rows
+  // a host call copies each row range to the host while the next is reduced
+  const bool pieces = p->host_out && !gid;
+  const int n_pieces = pieces ? (int)std::min<int64_t>(kHostPieces, n_bm) : 1;
+  const int64_t ncols = p->sep_n[1] * p->sep_n[2];
+  for (int k = 0; k < n_pieces; ++k) {
+    const int64_t b0 = n_bm * k / n_pieces, b1 = n_bm * (k + 1) / n_pieces;
+    const dim3 rgrid((unsigned)n_cb, (unsigned)(b1 - b0));
+    k_sep_reduce<<<rgrid, 256, 0, st>>>(
+        p->d.sep_partial, sep_part_floats(p->sep_mt, ncols), n_cb, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
+        (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)), p->d.sep_axis_s, p->d.sep_axis_lo, p->sep_n[0],
+        p->sep_n[1], p->sep_n[2],
+        make_float3((float)p->inst[0].H[0], (float)p->inst[0].H[1], (float)p->inst[0].H[2]), p->d.inst_shift, b0,
+        gid ? p->d.sep_virt : amp_out, gid ? nullptr : int_out);
+    p->last_launches += 1;
+    if (pieces) {
+      // h rows 16 b0 .. 16 b1 of the map: a contiguous range of points
+      const int64_t m0 = std::min<int64_t>(16 * b0, p->sep_n[0]) * ncols;
+      const int64_t m1 = std::min<int64_t>(16 * b1, p->sep_n[0]) * ncols;
+      cudaEventRecord(p->copy_ev[k], st);
+      cudaStreamWaitEvent(p->copy_stream, p->copy_ev[k], 0);
+      if (m1 > m0)
+        cudaMemcpyAsync(static_cast<float2*>(p->host_out) + m0, amp_out + m0, (size_t)(m1 - m0) * sizeof(float2),
+                        cudaMemcpyDeviceToHost, p->copy_stream);
+    }
+  }
+  if (pieces) {
+    // the caller's stream resumes once the last range is on the host
+    cudaEventRecord(p->copy_ev[kHostPieces], p->copy_stream);
+    cudaStreamWaitEvent(st, p->copy_ev[kHostPieces], 0);
+  }
   if (gid) {
     scatter_status s2 = launch_gid_combine(p, amp_out, int_out, st);
     if (s2 != SCATTER_OK) return s2;

@@ -1,0 +1,111 @@
+"""scatter_amplitude_host: host positions in, host map out, through the C ABI.
+
+On SEPARABLE grid plans the final reduction runs in row ranges and each
+range is copied to the host on the plan's second stream while the next is
+reduced; other plans copy the map after the forward.  Each case compares
+the host map with the FP64 oracle (the path's own tolerance) and with the
+device-buffer call on the same plan element by element (the same kernels on
+the same inputs: bitwise equal).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle
+from closed_forms import rel_l2
+from paper_1010_2641_gb300 import api
+from paper_1010_2641_gb300 import binding as B
+from paper_1010_2641_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+A_LAT = W.LATTICE_A
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _device_map(plan, xyz, occ=None):
+    A = plan.amplitude(torch.tensor(xyz, dtype=torch.float64, device="cuda:0"),
+                       None if occ is None else torch.tensor(occ, dtype=torch.float32, device="cuda:0"))
+    plan.check()
+    return A.cpu()
+
+
+# n0 = 40 -> 80 map rows -> three 32-row blocks: three ragged copy ranges;
+# n0 = 3 -> one block: one range; n0 = 128 -> eight blocks in four ranges
+@pytest.mark.parametrize("shape", [(40, 12, 20), (3, 33, 17), (128, 16, 8)])
+def test_separable_grid_ranges_copied_while_reducing(shape):
+    c = W.fcc_sphere(radius_cells=4.5, seed=71)
+    occ = np.random.default_rng(72).uniform(0.5, 1.0, len(c.xyz)).astype(np.float32)
+    axes = [W.linspace_axis(0.0, shape[0], step=0.004), W.linspace_axis(0.0, shape[1], step=0.004),
+            W.linspace_axis(4.0, shape[2], step=0.004)]
+    S = W.grid_points(axes)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="separable")
+    xyz_h = torch.tensor(c.xyz, dtype=torch.float64).pin_memory()
+    occ_h = torch.tensor(occ).pin_memory()
+    out = plan.amplitude_host(xyz_h, occ_h)
+    torch.cuda.synchronize()
+    plan.check()
+    assert out.device.type == "cpu" and out.is_pinned()
+    dev = _device_map(plan, c.xyz, occ)
+    assert torch.equal(out, dev)
+    ref = oracle.amplitude(c.xyz, S, c.coef, A_LAT, species=c.species, occ=occ)
+    assert rel_l2(out.numpy().astype(np.complex128), ref) < 1e-3
+
+
+def test_generic_list_with_pageable_buffers():
+    c = W.fcc_sphere(radius_cells=3.5, seed=73)
+    S = W.ewald_slice(3001, seed=74)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), s_list=S, atom_species=c.species)
+    out = torch.zeros(len(S), dtype=torch.complex64)  # pageable
+    plan.amplitude_host(c.xyz, out=out)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, _device_map(plan, c.xyz))
+    ref = oracle.amplitude(c.xyz, S, c.coef, A_LAT, species=c.species)
+    assert rel_l2(out.numpy().astype(np.complex128), ref) < 1e-4
+    # a second call into the same buffer (the plan's staging is reused)
+    moved = c.xyz + np.array([0.25, -0.5, 1.0])
+    plan.amplitude_host(moved, out=out)
+    torch.cuda.synchronize()
+    ref2 = oracle.amplitude(moved, S, c.coef, A_LAT, species=c.species)
+    assert rel_l2(out.numpy().astype(np.complex128), ref2) < 1e-4
+
+
+def test_bench_map_four_ranges_equal_the_device_call():
+    c = W.fcc_sphere()
+    axes = [W.linspace_axis(0.0, 256, step=0.002), W.linspace_axis(0.0, 256, step=0.002),
+            W.linspace_axis(4.0, 64, step=0.002)]
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, path="separable")
+    xyz_h = torch.tensor(c.xyz, dtype=torch.float64).pin_memory()
+    out = plan.amplitude_host(xyz_h)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, _device_map(plan, c.xyz))
+    # sampled points against the oracle (the map's 1e-4 metric tolerance)
+    idx = np.sort(np.random.default_rng(75).choice(256 * 256 * 64, 2048, replace=False))
+    S = W.grid_points(axes)[idx]
+    ref = oracle.amplitude(c.xyz, S, c.coef, A_LAT, species=c.species)
+    assert rel_l2(out.numpy()[idx].astype(np.complex128), ref) < 1e-4
+
+
+def test_rejects_device_buffers():
+    c = W.fcc_sphere(radius_cells=2.5, seed=76)
+    S = W.ewald_slice(100, seed=77)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), s_list=S, atom_species=c.species)
+    with pytest.raises(ValueError):
+        plan.amplitude_host(torch.tensor(c.xyz, dtype=torch.float64, device="cuda:0"))
+    # the C ABI itself: a device map pointer is INVALID_ARG
+    xyz_h = torch.tensor(c.xyz, dtype=torch.float64)
+    A_dev = torch.empty(len(S), dtype=torch.complex64, device="cuda:0")
+    st = B.lib().scatter_amplitude_host(plan._h, ctypes.c_void_p(xyz_h.data_ptr()), None,
+                                        ctypes.c_void_p(A_dev.data_ptr()), None)
+    assert st == 1  # SCATTER_ERR_INVALID_ARG
+    st = B.lib().scatter_amplitude_host(plan._h, None, None, ctypes.c_void_p(A_dev.data_ptr()), None)
+    assert st == 1
