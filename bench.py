@@ -570,6 +570,21 @@ def measure_paths(args, dev, clk, only=None):
                                "roofline": _rate_roof(len(cube.xyz) * 128 ** 3, ms, 16.0, n_sm, rc.get("clk"), "Gpair/s", "alu",
                                                       "pairs (8 FMA-pipe ops each)")}
         del plan, x, A, I_obs
+    if want('adjoint_list'):
+        # the S-list adjoint (k_adjoint: MUFU sin/cos per pair): strained sphere x an Ewald-slice list
+        c_l = W.fcc_sphere()
+        S_l = W.ewald_slice(262144, seed=8101)
+        plan = api.Plan(c_l.coef, W.LATTICE_A, len(c_l.xyz), s_list=S_l, atom_species=c_l.species, timing=True)
+        x = torch.tensor(c_l.xyz, dtype=torch.float64, device=dev)
+        I_obs = plan.intensity(torch.tensor(W.perturbed_copy(c_l).xyz, dtype=torch.float64, device=dev))
+        A = plan.amplitude(x)
+        ms = timed(lambda: plan.backward(x, A, I_obs), plan)
+        pairs_l = len(c_l.xyz) * len(S_l)
+        res["adjoint_list"] = {"value": pairs_l / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                               "workload": "strained sphere 134009 atoms x 262144 Ewald-slice points near (111), dL/dr",
+                               "roofline": _rate_roof(pairs_l, ms, MUFU_SINCOS_PER_SM_CLK / MUFU_OPS_PER_PAIR, n_sm,
+                                                      rc.get("clk"), "Gpair/s", "alu", "pairs (2 MUFU sin/cos each)")}
+        del plan, x, A, I_obs
     if want('adjoint_cube_separable'):
         # the same gradient on a SEPARABLE plan: the per-atom sums contract on the tensor cores
         cube = W.strained_cube()

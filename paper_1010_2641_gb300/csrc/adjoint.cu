@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <type_traits>
 #include "device_common.cuh"
 #include "launch.h"
 
@@ -160,9 +161,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     z[r] = at.z;
     c[r] = at.w;
   }
-  double gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
-#pragma unroll
-  for (int r = 0; r < kAdjRA; ++r) gx[r] = gy[r] = gz[r] = 0.0;
+  // outer sums over the tiles: double-float on the FP32 pipe
+  dev::DFloatSum gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
 
   if (tid == 0) {
     dev::mbar_init(&sh_bar[0], 1);
@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     float ax[kAdjRA], ay[kAdjRA], az[kAdjRA];
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) ax[r] = ay[r] = az[r] = 0.f;
-    if (ok) {
+    // one loop body per phase form: the choice stays out of the unrolled
+    // pair loop, whose eight atoms' chains then interleave freely
+    auto tile = [&](auto exact_tag) {
+      constexpr bool kExact = decltype(exact_tag)::value;
       const float4* sv = sh_s[st];
 #pragma unroll 2
       for (int j = 0; j < cnt; ++j) {
@@ -202,9 +205,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
 #pragma unroll
         for (int r = 0; r < kAdjRA; ++r) {
           const float f =
-              exact ? dev::frac_rn(dev::frac_product_plus(
-                          p.x, x[r], dev::frac_product_plus(p.y, y[r], dev::frac_product_plus(p.z, z[r], c[r]))))
-                    : dev::frac_rn(fmaf(p.z, z[r], fmaf(p.y, y[r], fmaf(p.x, x[r], c[r]))));
+              kExact ? dev::frac_rn(dev::frac_product_plus(
+                           p.x, x[r], dev::frac_product_plus(p.y, y[r], dev::frac_product_plus(p.z, z[r], c[r]))))
+                     : dev::frac_rn(fmaf(p.z, z[r], fmaf(p.y, y[r], fmaf(p.x, x[r], c[r]))));
           float sn, cs;
           dev::sincos_cycles_mufu(f, &sn, &cs);
           const float v = fmaf(p.w, sn, q.w * cs);
@@ -213,12 +216,18 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
           az[r] = fmaf(q.z, v, az[r]);
         }
       }
+    };
+    if (ok) {
+      if (exact)
+        tile(std::true_type{});
+      else
+        tile(std::false_type{});
     }
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) {
-      gx[r] += ax[r];
-      gy[r] += ay[r];
-      gz[r] += az[r];
+      gx[r].add(ax[r]);
+      gy[r].add(ay[r]);
+      gz[r].add(az[r]);
     }
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -238,9 +247,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     const int i = r * kAdjThreads + tid;
     if (i < blk.count) {
       const int64_t slot = blk.begin + i;
-      out[3 * slot] = (float)gx[r];
-      out[3 * slot + 1] = (float)gy[r];
-      out[3 * slot + 2] = (float)gz[r];
+      out[3 * slot] = gx[r].value();
+      out[3 * slot + 1] = gy[r].value();
+      out[3 * slot + 2] = gz[r].value();
     }
   }
 }
