@@ -161,6 +161,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     z[r] = at.z;
     c[r] = at.w;
   }
+  // the atoms in packed pairs for the plain phase form
+  unsigned long long x2[kAdjRA / 2], y2[kAdjRA / 2], z2[kAdjRA / 2], c2[kAdjRA / 2];
+#pragma unroll
+  for (int pp = 0; pp < kAdjRA / 2; ++pp) {
+    x2[pp] = dev::pack2(x[2 * pp], x[2 * pp + 1]);
+    y2[pp] = dev::pack2(y[2 * pp], y[2 * pp + 1]);
+    z2[pp] = dev::pack2(z[2 * pp], z[2 * pp + 1]);
+    c2[pp] = dev::pack2(c[2 * pp], c[2 * pp + 1]);
+  }
   // outer sums over the tiles: double-float on the FP32 pipe
   dev::DFloatSum gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
 
@@ -198,6 +207,45 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     auto tile = [&](auto exact_tag) {
       constexpr bool kExact = decltype(exact_tag)::value;
       const float4* sv = sh_s[st];
+      if (!kExact) {
+        // two atoms per packed register pair: every step of the plain form is
+        // elementwise over the atoms, so one f32x2 operation does two atoms'
+        // (the same roundings as the scalar fmaf / __fadd_rn / __fmul_rn);
+        // the point's values are broadcast into both halves
+        using u64 = unsigned long long;
+        const u64 magic2 = dev::pack2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: rint by addition
+        const u64 twopi2 = dev::pack2(6.28318530717958647692f, 6.28318530717958647692f);
+        u64 ax2[kAdjRA / 2], ay2[kAdjRA / 2], az2[kAdjRA / 2];
+#pragma unroll
+        for (int pp = 0; pp < kAdjRA / 2; ++pp) ax2[pp] = ay2[pp] = az2[pp] = 0ull;
+#pragma unroll 2
+        for (int j = 0; j < cnt; ++j) {
+          const float4 p = sv[2 * j];      // s, gF.re
+          const float4 q = sv[2 * j + 1];  // S, gF.im
+          const u64 px = dev::pack2(p.x, p.x), py = dev::pack2(p.y, p.y), pz = dev::pack2(p.z, p.z);
+          const u64 pw = dev::pack2(p.w, p.w), qw = dev::pack2(q.w, q.w);
+          const u64 qx = dev::pack2(q.x, q.x), qy = dev::pack2(q.y, q.y), qz = dev::pack2(q.z, q.z);
+#pragma unroll
+          for (int pp = 0; pp < kAdjRA / 2; ++pp) {
+            const u64 ph = dev::fma2(pz, z2[pp], dev::fma2(py, y2[pp], dev::fma2(px, x2[pp], c2[pp])));
+            const u64 f = dev::sub2(ph, dev::sub2(dev::add2(ph, magic2), magic2));  // ph - rint(ph)
+            float t0, t1;
+            dev::unpack2(dev::mul2(f, twopi2), t0, t1);
+            const u64 sn = dev::pack2(__sinf(t0), __sinf(t1)), cs = dev::pack2(__cosf(t0), __cosf(t1));
+            const u64 v = dev::fma2(pw, sn, dev::mul2(qw, cs));
+            ax2[pp] = dev::fma2(qx, v, ax2[pp]);
+            ay2[pp] = dev::fma2(qy, v, ay2[pp]);
+            az2[pp] = dev::fma2(qz, v, az2[pp]);
+          }
+        }
+#pragma unroll
+        for (int pp = 0; pp < kAdjRA / 2; ++pp) {
+          dev::unpack2(ax2[pp], ax[2 * pp], ax[2 * pp + 1]);
+          dev::unpack2(ay2[pp], ay[2 * pp], ay[2 * pp + 1]);
+          dev::unpack2(az2[pp], az[2 * pp], az[2 * pp + 1]);
+        }
+        return;
+      }
 #pragma unroll 2
       for (int j = 0; j < cnt; ++j) {
         const float4 p = sv[2 * j];      // s, gF.re
