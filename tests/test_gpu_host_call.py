@@ -109,3 +109,44 @@ def test_rejects_device_buffers():
     assert st == 1  # SCATTER_ERR_INVALID_ARG
     st = B.lib().scatter_amplitude_host(plan._h, None, None, ctypes.c_void_p(A_dev.data_ptr()), None)
     assert st == 1
+
+
+@pytest.mark.parametrize("path,tol", [("separable", 1e-3), ("generic", 1e-4)])
+def test_grazing_incidence_map(path, tol):
+    """GID plans copy the map after the forward (the separable route's beams
+    are combined after the reduction, so its map is not copied in ranges)."""
+    c = W.truncated_pyramid(base_cells=12, height_cells=5, top_cells=4)
+    axes = [np.linspace(3.8, 4.05, 24), np.linspace(-0.125, 0.125, 20), np.deg2rad((np.arange(32) + 1) / 32)]
+    gid = dict(wavelength=W.WAVELENGTH_10KEV, alpha_i=W.GID_ALPHA_I, delta=W.GID_DELTA, beta=W.GID_BETA)
+    plan = api.Plan(c.coef, A_LAT, len(c.xyz), axes=axes, atom_species=c.species, gid=gid, path=path)
+    out = plan.amplitude_host(torch.tensor(c.xyz, dtype=torch.float64).pin_memory())
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, _device_map(plan, c.xyz))
+    ref = oracle.dwba(c.xyz, W.grid_points(axes), c.coef, A_LAT, W.WAVELENGTH_10KEV, W.GID_ALPHA_I, W.GID_DELTA,
+                      W.GID_BETA, species=c.species)
+    assert rel_l2(out.numpy().astype(np.complex128), ref) < tol
+
+
+def test_batch_of_uneven_instances():
+    """A batch (persistent launch, per-instance offsets) through the host call;
+    every instance against the oracle."""
+    xyzs, sps, Ss = [], [], []
+    for b, (r, m) in enumerate([(2.5, 700), (4.0, 1500), (1.5, 300)]):
+        c = W.fcc_sphere(radius_cells=r, seed=80 + b)
+        xyzs.append(c.xyz)
+        sps.append(c.species)
+        Ss.append(W.ewald_slice(m, seed=90 + b))
+    coef = W.fcc_sphere(radius_cells=1.5, seed=80).coef
+    ao = np.concatenate([[0], np.cumsum([len(x) for x in xyzs])]).astype(np.int64)
+    so = np.concatenate([[0], np.cumsum([len(s) for s in Ss])]).astype(np.int64)
+    xyz, sp, S = np.concatenate(xyzs), np.concatenate(sps), np.concatenate(Ss)
+    plan = api.Plan(coef, A_LAT, len(xyz), s_list=S, atom_species=sp, atom_off=ao, s_off=so)
+    out = plan.amplitude_host(xyz)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(out, _device_map(plan, xyz))
+    A = out.numpy().astype(np.complex128)
+    for b in range(3):
+        ref = oracle.amplitude(xyz[ao[b]:ao[b + 1]], S[so[b]:so[b + 1]], coef, A_LAT, species=sp[ao[b]:ao[b + 1]])
+        assert rel_l2(A[so[b]:so[b + 1]], ref) < 1e-4, b
