@@ -141,7 +141,44 @@ struct AdjArgs {
   unsigned* status;
 };
 
-__global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
+// Outer sums of a thread's atoms (over S tiles), double-float, in shared
+// memory: hi and lo of component d of the thread's atom r at [d][r][thread].
+// Every thread owns its slots (no synchronisation) and consecutive threads
+// use consecutive words; a slot is touched once per tile, so keeping the
+// 3 x kAdjRA pairs out of the registers costs little and lets four CTAs
+// share an SM.
+struct OuterSums {
+  float2 (*g)[kAdjRA][kAdjThreads];
+  int t;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int r = 0; r < kAdjRA; ++r) g[d][r][t] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void add(int d, int r, float x) {
+    const float2 v = g[d][r][t];
+    dev::DFloatSum a;
+    a.hi = v.x;
+    a.lo = v.y;
+    a.add(x);
+    g[d][r][t] = make_float2(a.hi, a.lo);
+  }
+  __device__ __forceinline__ void add_product(int d, int r, float x, float y) {
+    const float2 v = g[d][r][t];
+    dev::DFloatSum a;
+    a.hi = v.x;
+    a.lo = v.y;
+    a.add_product(x, y);
+    g[d][r][t] = make_float2(a.hi, a.lo);
+  }
+  __device__ __forceinline__ float value(int d, int r) const {
+    const float2 v = g[d][r][t];
+    return __fadd_rn(v.x, v.y);
+  }
+};
+
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adjoint(const AdjArgs a) {
   __shared__ __align__(128) float4 sh_s[2][kSTile * 2];
   __shared__ __align__(8) uint64_t sh_bar[2];
   const int tid = threadIdx.x;
@@ -170,8 +207,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     z2[pp] = dev::pack2(z[2 * pp], z[2 * pp + 1]);
     c2[pp] = dev::pack2(c[2 * pp], c[2 * pp + 1]);
   }
-  // outer sums over the tiles: double-float on the FP32 pipe
-  dev::DFloatSum gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
+  // outer sums over the tiles: double-float on the FP32 pipe, in shared memory
+  __shared__ float2 sh_g[3][kAdjRA][kAdjThreads];
+  OuterSums g{sh_g, tid};
+  g.zero();
 
   if (tid == 0) {
     dev::mbar_init(&sh_bar[0], 1);
@@ -273,9 +312,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     }
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) {
-      gx[r].add(ax[r]);
-      gy[r].add(ay[r]);
-      gz[r].add(az[r]);
+      g.add(0, r, ax[r]);
+      g.add(1, r, ay[r]);
+      g.add(2, r, az[r]);
     }
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -295,9 +334,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a) {
     const int i = r * kAdjThreads + tid;
     if (i < blk.count) {
       const int64_t slot = blk.begin + i;
-      out[3 * slot] = gx[r].value();
-      out[3 * slot + 1] = gy[r].value();
-      out[3 * slot + 2] = gz[r].value();
+      out[3 * slot] = g.value(0, r);
+      out[3 * slot + 1] = g.value(1, r);
+      out[3 * slot + 2] = g.value(2, r);
     }
   }
 }
@@ -330,7 +369,7 @@ struct AdjLineArgs {
 
 constexpr int kReseed = 64;  // points between exact re-seeds of the recurrence
 
-__global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adjoint_line(const AdjLineArgs a) {
   __shared__ __align__(128) float4 sh_s[2][kSTile];
   __shared__ __align__(8) uint64_t sh_bar[2];
   const int tid = threadIdx.x;
@@ -356,8 +395,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     wr[r] = cs;
     wi[r] = sn;
   }
-  // outer sums over the lines: double-float on the FP32 pipe
-  dev::DFloatSum gx[kAdjRA], gy[kAdjRA], gz[kAdjRA];
+  // outer sums over the lines: double-float on the FP32 pipe, in shared memory
+  __shared__ float2 sh_g[3][kAdjRA][kAdjThreads];
+  OuterSums g{sh_g, tid};
+  g.zero();
 
   if (tid == 0) {
     dev::mbar_init(&sh_bar[0], 1);
@@ -446,9 +487,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     const float Sx = a.H[0] + sx, Sy = a.H[1] + sy;
 #pragma unroll
     for (int r = 0; r < kAdjRA; ++r) {
-      gx[r].add_product(Sx, sv[r]);
-      gy[r].add_product(Sy, sv[r]);
-      gz[r].add(szv[r]);
+      g.add_product(0, r, Sx, sv[r]);
+      g.add_product(1, r, Sy, sv[r]);
+      g.add(2, r, szv[r]);
     }
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -468,9 +509,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_line(const AdjLineArgs 
     const int i = r * kAdjThreads + tid;
     if (i < blk.count) {
       const int64_t slot = blk.begin + i;
-      out[3 * slot] = gx[r].value();
-      out[3 * slot + 1] = gy[r].value();
-      out[3 * slot + 2] = gz[r].value();
+      out[3 * slot] = g.value(0, r);
+      out[3 * slot + 1] = g.value(1, r);
+      out[3 * slot + 2] = g.value(2, r);
     }
   }
 }
