@@ -55,39 +55,83 @@ __device__ __forceinline__ void atompar_sums(const float4* sh_s, const float4* s
                                              const float (&y)[K], const float (&z)[K], const float (&c)[K],
                                              const float (&w)[K], const float4* __restrict__ lo_base, int nk,
                                              float2 (*sh_part)[kApPts], int lane, int warp) {
-  for (int p = 0; p < np; ++p) {
-    const float4 s = sh_s[p];
-    const float4 sl = EXACT ? sh_slo[p] : s;
-    // two accumulator pairs halve the dependent FFMA chain
-    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+  if constexpr (!EXACT && K % 2 == 0) {
+    // two atoms per packed register pair (atoms 2k and 2k + 1 in the low and
+    // high halves): every step is elementwise over the atoms and rounds like
+    // its scalar form, and the halves of the packed sums are exactly the two
+    // accumulator pairs (even and odd atoms) of the scalar loop below
+    using u64 = unsigned long long;
+    constexpr int KP = K / 2 > 0 ? K / 2 : 1;
+    u64 x2[KP], y2[KP], z2[KP], c2[KP], w2[KP];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (EXACT && k < nk) e = __ldg(lo_base + k * kApThreads);  // slots past the block's end: weight 0
-      const float f = EXACT ? dev::frac_rn(dev::frac_product2_plus(
-                                  s.x, sl.x, x[k],
-                                  dev::frac_product2_plus(
-                                      s.y, sl.y, y[k],
-                                      dev::frac_product2_plus(s.z, sl.z, z[k],
-                                                              fmaf(s.x, e.x, fmaf(s.y, e.y, fmaf(s.z, e.z, c[k])))))))
-                            : dev::frac_rn(fmaf(s.z, z[k], fmaf(s.y, y[k], fmaf(s.x, x[k], c[k]))));
-      float sn, cs;
-      dev::sincos_cycles_mufu(f, &sn, &cs);
-      if (k & 1) {
-        re1 = fmaf(w[k], cs, re1);
-        im1 = fmaf(w[k], sn, im1);
-      } else {
-        re0 = fmaf(w[k], cs, re0);
-        im0 = fmaf(w[k], sn, im0);
+    for (int k = 0; k < KP; ++k) {
+      x2[k] = dev::pack2(x[2 * k], x[2 * k + 1]);
+      y2[k] = dev::pack2(y[2 * k], y[2 * k + 1]);
+      z2[k] = dev::pack2(z[2 * k], z[2 * k + 1]);
+      c2[k] = dev::pack2(c[2 * k], c[2 * k + 1]);
+      w2[k] = dev::pack2(w[2 * k], w[2 * k + 1]);
+    }
+    const u64 magic2 = dev::pack2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: rint by addition
+    const u64 twopi2 = dev::pack2(6.28318530717958647692f, 6.28318530717958647692f);
+    for (int p = 0; p < np; ++p) {
+      const float4 s = sh_s[p];
+      const u64 sx = dev::pack2(s.x, s.x), sy = dev::pack2(s.y, s.y), sz = dev::pack2(s.z, s.z);
+      u64 re2 = 0ull, im2 = 0ull;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        const u64 ph = dev::fma2(sz, z2[k], dev::fma2(sy, y2[k], dev::fma2(sx, x2[k], c2[k])));
+        const u64 f = dev::sub2(ph, dev::sub2(dev::add2(ph, magic2), magic2));  // ph - rint(ph)
+        float t0, t1;
+        dev::unpack2(dev::mul2(f, twopi2), t0, t1);
+        re2 = dev::fma2(w2[k], dev::pack2(__cosf(t0), __cosf(t1)), re2);
+        im2 = dev::fma2(w2[k], dev::pack2(__sinf(t0), __sinf(t1)), im2);
       }
-    }
-    float re = re0 + re1, im = im0 + im1;
+      float re0, re1, im0, im1;
+      dev::unpack2(re2, re0, re1);
+      dev::unpack2(im2, im0, im1);
+      float re = re0 + re1, im = im0 + im1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) sh_part[warp][p] = make_float2(re, im);
     }
-    if (lane == 0) sh_part[warp][p] = make_float2(re, im);
+  } else {
+    for (int p = 0; p < np; ++p) {
+      const float4 s = sh_s[p];
+      const float4 sl = EXACT ? sh_slo[p] : s;
+      // two accumulator pairs halve the dependent FFMA chain
+      float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (EXACT && k < nk) e = __ldg(lo_base + k * kApThreads);  // slots past the block's end: weight 0
+        const float f = EXACT ? dev::frac_rn(dev::frac_product2_plus(
+                                    s.x, sl.x, x[k],
+                                    dev::frac_product2_plus(
+                                        s.y, sl.y, y[k],
+                                        dev::frac_product2_plus(s.z, sl.z, z[k],
+                                                                fmaf(s.x, e.x, fmaf(s.y, e.y, fmaf(s.z, e.z, c[k])))))))
+                              : dev::frac_rn(fmaf(s.z, z[k], fmaf(s.y, y[k], fmaf(s.x, x[k], c[k]))));
+        float sn, cs;
+        dev::sincos_cycles_mufu(f, &sn, &cs);
+        if (k & 1) {
+          re1 = fmaf(w[k], cs, re1);
+          im1 = fmaf(w[k], sn, im1);
+        } else {
+          re0 = fmaf(w[k], cs, re0);
+          im0 = fmaf(w[k], sn, im0);
+        }
+      }
+      float re = re0 + re1, im = im0 + im1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) sh_part[warp][p] = make_float2(re, im);
+    }
   }
 }
 
