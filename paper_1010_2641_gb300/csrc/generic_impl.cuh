@@ -102,7 +102,56 @@ __device__ __forceinline__ bool chunk_sum(const float4* __restrict__ atom4, cons
     float2 acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
-    if (ok) {
+    if (ok && !EXACT && R % 2 == 0) {
+      // the plain phase for two points per packed register pair: each half
+      // runs one point's operations with the scalar form's roundings (the
+      // atom's values broadcast into both halves), so every point's sum is
+      // the scalar loop's bit for bit, in half the issue slots
+      using u64 = unsigned long long;
+      constexpr int RP = R / 2 > 0 ? R / 2 : 1;
+      const float4* at4 = sh_atom[st];
+      const float* atw = sh_w[st];
+      const u64 magic2 = dev::pack2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: rint by addition
+      const u64 twopi2 = dev::pack2(6.28318530717958647692f, 6.28318530717958647692f);
+      u64 px[RP], py[RP], pz[RP], are[RP], aim[RP];
+#pragma unroll
+      for (int q = 0; q < RP; ++q) {
+        px[q] = dev::pack2(sx[2 * q], sx[2 * q + 1]);
+        py[q] = dev::pack2(sy[2 * q], sy[2 * q + 1]);
+        pz[q] = dev::pack2(sz[2 * q], sz[2 * q + 1]);
+        are[q] = aim[q] = 0ull;
+      }
+#pragma unroll 2
+      for (int j = 0; j < cnt; ++j) {
+        const float4 at = at4[j];
+        const float w = atw[j];
+        const u64 w2 = dev::pack2(w, w), az = dev::pack2(at.z, at.z);
+        u64 b2 = 0ull, ax = 0ull, ay = 0ull, aw = 0ull;
+        if (MODE == kModeGrid) {
+          const float base = fmaf(sy[0], at.y, fmaf(sx[0], at.x, at.w));
+          b2 = dev::pack2(base, base);
+        } else {
+          ax = dev::pack2(at.x, at.x);
+          ay = dev::pack2(at.y, at.y);
+          aw = dev::pack2(at.w, at.w);
+        }
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+          const u64 ph = MODE == kModeGrid ? dev::fma2(pz[q], az, b2)
+                                           : dev::fma2(pz[q], az, dev::fma2(py[q], ay, dev::fma2(px[q], ax, aw)));
+          const u64 f = dev::sub2(ph, dev::sub2(dev::add2(ph, magic2), magic2));  // ph - rint(ph)
+          float t0, t1;
+          dev::unpack2(dev::mul2(f, twopi2), t0, t1);
+          are[q] = dev::fma2(w2, dev::pack2(__cosf(t0), __cosf(t1)), are[q]);
+          aim[q] = dev::fma2(w2, dev::pack2(__sinf(t0), __sinf(t1)), aim[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RP; ++q) {
+        dev::unpack2(are[q], acc[2 * q].x, acc[2 * q + 1].x);
+        dev::unpack2(aim[q], acc[2 * q].y, acc[2 * q + 1].y);
+      }
+    } else if (ok) {
       const float4* at4 = sh_atom[st];
       const float4* atl = sh_lo[st];
       const float* atw = sh_w[st];
