@@ -469,10 +469,11 @@ def measure_paths(args, dev, clk, only=None):
     def timed(fn, plan, reps=2):
         """_time_calls over at least 0.5 s, with the SM clocks sampled while
         the calls ran kept in rc["clk"]: each row's roofline takes the clock
-        its own kernel ran at."""
+        its own kernel ran at.  --reps R: exactly R timed calls after the
+        warm-up (a fixed launch sequence, for profilers)."""
         cs = ClockSampler(0, args.log_dir)
         cs.start()
-        ms = _time_calls(fn, plan, reps, min_s=0.5)
+        ms = _time_calls(fn, plan, args.reps, min_s=0.0) if args.reps else _time_calls(fn, plan, reps, min_s=0.5)
         rc["clk"] = cs.stop()
         return ms
 
@@ -771,6 +772,8 @@ def main():
     ap.add_argument("--grid", default=None, help="smaller S grid n0,n1,n2 (profiling cases)")
     ap.add_argument("--sweep", default=None, help="speed sweep over atoms x reflections, e.g. 100,1000,10000")
     ap.add_argument("--row", default=None, help="run one row of the paths section alone (profiling), e.g. adjoint_cube")
+    ap.add_argument("--reps", type=int, default=0,
+                    help="paths rows: exactly this many timed calls per row (a fixed launch sequence for profiling)")
     ap.add_argument("--path", default="separable", choices=["generic", "separable"],
                     help="kernel family of the headline line (both meet the 1e-4 tolerance on this map)")
     args = ap.parse_args()

@@ -764,17 +764,19 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
       // h rows 16 b0 .. 16 b1 of the map: a contiguous range of points
       const int64_t m0 = std::min<int64_t>(16 * b0, p->sep_n[0]) * ncols;
       const int64_t m1 = std::min<int64_t>(16 * b1, p->sep_n[0]) * ncols;
-      cudaEventRecord(p->copy_ev[k], st);
-      cudaStreamWaitEvent(p->copy_stream, p->copy_ev[k], 0);
-      if (m1 > m0)
-        cudaMemcpyAsync(static_cast<float2*>(p->host_out) + m0, amp_out + m0, (size_t)(m1 - m0) * sizeof(float2),
-                        cudaMemcpyDeviceToHost, p->copy_stream);
+      cudaError_t e = cudaEventRecord(p->copy_ev[k], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_stream, p->copy_ev[k], 0);
+      if (e == cudaSuccess && m1 > m0)
+        e = cudaMemcpyAsync(static_cast<float2*>(p->host_out) + m0, amp_out + m0, (size_t)(m1 - m0) * sizeof(float2),
+                            cudaMemcpyDeviceToHost, p->copy_stream);
+      if (e != cudaSuccess) return cuda_status(e, "map range to the host");
     }
   }
   if (pieces) {
     // the caller's stream resumes once the last range is on the host
-    cudaEventRecord(p->copy_ev[kHostPieces], p->copy_stream);
-    cudaStreamWaitEvent(st, p->copy_ev[kHostPieces], 0);
+    cudaError_t e = cudaEventRecord(p->copy_ev[kHostPieces], p->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->copy_ev[kHostPieces], 0);
+    if (e != cudaSuccess) return cuda_status(e, "host copy completion");
   }
   if (gid) {
     scatter_status s2 = launch_gid_combine(p, amp_out, int_out, st);
