@@ -506,8 +506,11 @@ def measure_paths(args, dev, clk, only=None):
         plan = api.Plan(c.coef, W.LATTICE_A, n_atoms, axes=axes, atom_species=c.species, timing=True)
         xa = torch.tensor(c.xyz, dtype=torch.float64, device=dev)
         ms = timed(lambda: plan.amplitude(xa), plan)
+        ms_call = _time_whole(lambda: plan.amplitude(xa))
         inf = plan.info()
-        res["auto_sphere"] = {"value": n_atoms * n_s / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+        # value from whole calls (every kernel of the call), like the headline's steps
+        res["auto_sphere"] = {"value": n_atoms * n_s / (ms_call * 1e-3), "unit": UNIT, "call_ms": ms_call,
+                              "kernel_ms": ms,
                               "path_chosen": {1: "generic", 2: "separable"}.get(inf["path"], str(inf["path"])),
                               "workload": "strained sphere, full map, default options (AUTO, tolerance 1e-4)",
                               "clocks": rc.get("clk")}
