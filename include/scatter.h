@@ -156,8 +156,12 @@ typedef struct scatter_problem {
    *      transmitted in and out, W = T_i T_f, refracted and attenuated in
    *      the medium: exp(2 i pi (h x + k y + sigma z)), sigma =
    *      (a / lambda)(conj q_i + conj q_f), q = sqrt(n^2 - cos^2 alpha),
-   *      f at the vacuum beam S_1.  Generic and FP64 paths (the separable
-   *      path's formed rows are unit-modulus phases).                      */
+   *      f at the vacuum beam S_1.  Generic and FP64 paths; the separable
+   *      path when asked for (SCATTER_PATH_SEPARABLE; AUTO keeps the generic
+   *      path): one beam on the virtual l axis, its formed rows carrying
+   *      exp(-2 pi Im(sigma) z') of the centred z', which must stay below
+   *      e^10 (a call whose crystal is too tall for the attenuation of its
+   *      exit angles reports SCATTER_ERR_NUMERIC at scatter_check).        */
   int32_t gid_mode;
 } scatter_problem;
 

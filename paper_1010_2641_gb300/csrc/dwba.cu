@@ -371,18 +371,18 @@ __global__ void __launch_bounds__(128) k_f64_gid(const double* __restrict__ xyz,
   if (out_int) out_int[m] = (float)(are * are + aim * aim);
 }
 
-// Four-beam combination of a map computed on the virtual grid
-// (h, k, [Sz1 | Sz2 | -Sz2 | -Sz1] x alpha_f):  A = sum_t W_t(alpha_f) T_t.
-// f_s(|S_t|) and the translation phase are already in T.
+// Beam combination of a map computed on the virtual grid (h, k, beams x
+// alpha_f): [Sz1 | Sz2 | -Sz2 | -Sz1] on the substrate, [Re sigma] for a
+// buried object:  A = sum_t W_t(alpha_f) T_t.  f_s(|S_t|), the translation
+// phase and (buried) the attenuation are already in T.
 __global__ void k_gid_combine(const float2* __restrict__ virt, const float2* __restrict__ w, int64_t n_hk,
-                              int64_t n_af, float2* out_amp, float* out_int) {
+                              int64_t n_af, int n_beams, float2* out_amp, float* out_int) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_hk * n_af) return;
   const int64_t af = m % n_af, hk = m / n_af;
-  const float2* row = virt + hk * 4 * n_af + af;
+  const float2* row = virt + hk * n_beams * n_af + af;
   float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < n_beams; ++t) {
     const float2 c = dev::cmul(w[t * n_af + af], row[t * n_af]);
     v.x += c.x;
     v.y += c.y;
@@ -393,8 +393,8 @@ __global__ void k_gid_combine(const float2* __restrict__ virt, const float2* __r
 
 scatter_status launch_gid_combine(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st) {
   const int64_t n_hk = p->n_axis[0] * p->n_axis[1], n_af = p->n_axis[2];
-  k_gid_combine<<<(unsigned)((n_hk * n_af + 255) / 256), 256, 0, st>>>(p->d.sep_virt, p->d.gid_w, n_hk, n_af, amp_out,
-                                                                      int_out);
+  k_gid_combine<<<(unsigned)((n_hk * n_af + 255) / 256), 256, 0, st>>>(p->d.sep_virt, p->d.gid_w, n_hk, n_af,
+                                                                      (int)p->sep_beams, amp_out, int_out);
   p->last_launches += 1;
   return cuda_status(cudaGetLastError(), "gid combine launch");
 }
@@ -493,6 +493,8 @@ scatter_status prepare_gid(scatter_plan_s* p) {
     return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
   p->gid_sz_host = sz64;
+  p->gid_sz_im_host = sz64_im;
+  p->gid_szf_host = szf64;
   if ((e = up((void**)&p->d.gid_sz, sz.data(), sz.size() * sizeof(float))) != cudaSuccess) return cuda_status(e, "gid");
   if ((e = up((void**)&p->d.gid_sz_lo, sz_lo.data(), sz_lo.size() * sizeof(float))) != cudaSuccess)
     return cuda_status(e, "gid");

@@ -91,8 +91,6 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
         pr->delta < 0 || pr->beta < 0)
       return fail(SCATTER_ERR_INVALID_ARG, "invalid alpha_i/delta/beta");
     if (pr->gid_mode != 0 && pr->gid_mode != 1) return fail(SCATTER_ERR_INVALID_ARG, "gid_mode must be 0 or 1");
-    if (pr->gid_mode == 1 && op && op->path == SCATTER_PATH_SEPARABLE)
-      return fail(SCATTER_ERR_UNSUPPORTED, "a buried object (gid_mode 1) runs on the generic or FP64 path");
   }
   if (pr->center_mode != 0 && pr->center_mode != 1)
     return fail(SCATTER_ERR_INVALID_ARG, "center_mode must be 0 or 1");
@@ -328,6 +326,8 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);
   if (p->ev_end) cudaEventDestroy(p->ev_end);
   release(d.host_xyz);
+  release(d.sep_att);
+  release(d.sep_szf);
   release(d.host_occ);
   release(d.host_amp);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);

@@ -156,6 +156,9 @@ struct DeviceBuffers {
   double* host_xyz = nullptr;       // [n_atoms][3]
   float* host_occ = nullptr;        // [n_atoms]
   float2* host_amp = nullptr;       // [n_s]
+  // separable path of a buried object: per virtual l column
+  float* sep_att = nullptr;         // 2 pi Im(sigma): the formed rows carry exp(-sep_att z')
+  float* sep_szf = nullptr;         // S_z of the column's form factor (the vacuum beam S_1)
 };
 
 }  // namespace scatter
@@ -207,6 +210,9 @@ struct scatter_plan_s {
   float sep_smax[2] = {0.f, 0.f};               // max |s| of the separable grid's b and c axes
   int32_t ap_n_blocks = 0;
   std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
+  std::vector<double> gid_sz_im_host;            // [n_af] Im sigma of a buried object's beam
+  std::vector<double> gid_szf_host;              // [4][n_af] S_z of each beam's form factor
+  int32_t sep_beams = 4;                         // beams stacked on the separable l axis (buried: 1)
   bool adj_ready = false;
   int adj_split = 1;
   int adj_blocks = 0;

@@ -31,6 +31,9 @@ constexpr int kSepTStages = 8;             // K-record ring (256 B per step)
 constexpr size_t kSepSmem = kSepAStages * kSepPair * kSepABytes + kSepBStages * kSepBBytes + 1024;  // + align
 constexpr uint32_t kSepTmemCols = 512;     // two 128 x 256 FP32 accumulators
 constexpr double kSepPhaseLim = 16.0;      // cycles: B phases below this skip the mod-1 reduction
+// largest exponent of a formed row's attenuation exp(-2 pi Im(sigma) z'): e^10
+// keeps hi + lo inside f16's range; beyond it the call reports NUMERIC
+constexpr float kSepAttMax = 10.0f;
 
 // -------------------------------------------------------------------------
 // descriptors (PTX tcgen05 shared-memory and instruction descriptors)
@@ -107,6 +110,8 @@ struct SepArgs {
   int64_t chunk_floats;   // floats of one chunk's partials (sep_part_floats)
   float* partial;         // [chunk] blocked as sep_part_off, raw D (no f_s)
   unsigned* status;
+  const float* axis_att;  // forward of a buried object: per l, 2 pi Im(sigma); the formed
+                          // rows carry exp(-axis_att[l] z'); null otherwise
 };
 
 // Partials in the accumulator's own blocking.  D row m (TMEM lane of its M

@@ -313,6 +313,8 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
     const int64_t col = col_base + (int64_t)rank * kPairHalfN + c_loc;
     const bool row_ok = col < col_end;
     float sb, sc, sbl = 0.f, scl = 0.f;  // sbl, scl: low parts of a double-float s (forward)
+    float att = 0.f;                     // buried object: 2 pi Im(sigma) of the column's beam
+    bool att_over = false;               // an attenuation exponent passed kSepAttMax
     if (a.ntiles) {
       const float4 at = row_ok ? a.atom4[col] : make_float4(0.f, 0.f, 0.f, 0.f);
       sb = at.y;
@@ -321,6 +323,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       const int64_t rb = row_ok ? col / a.n2 : 0, rc = row_ok ? col % a.n2 : 0;
       sb = a.axis_s[a.n0 + rb];
       sc = a.axis_s[a.n0 + a.n1 + rc];
+      if (a.axis_att) att = a.axis_att[rc];
       if (a.axis_lo) {
         sbl = a.axis_lo[a.n0 + rb];
         scl = a.axis_lo[a.n0 + a.n1 + rc];
@@ -359,8 +362,10 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       unsigned char* sB = ringB + bst * kPairBBytes;
       const float4* at = ring_atom[tst] + half * 8;
       // mode 0: raw phase, 1: reduced mod 1, 2: exact products, reduced
-      auto form = [&](auto mode_tag) {
+      // kAtt: a buried object's rows carry exp(-att z')
+      auto form = [&](auto mode_tag, auto att_tag) {
         constexpr int kMode = decltype(mode_tag)::value;
+        constexpr bool kAtt = decltype(att_tag)::value;
 #pragma unroll
         for (int kq = 0; kq < 2; ++kq) {
           uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
@@ -375,6 +380,16 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
                                : fmaf(sb, v.y, fmaf(sc, v.z, v.w));
               float sn, cs;
               dev::sincos_cycles_mufu(ph, &sn, &cs);
+              if (kAtt) {
+                float ex = -att * v.z;
+                if (ex > kSepAttMax) {
+                  ex = kSepAttMax;
+                  att_over = true;
+                }
+                const float gz = __expf(ex);
+                sn *= gz;
+                cs *= gz;
+              }
               split2(cs, sn, hi[q], lo[q]);
             }
           }
@@ -383,12 +398,18 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
           *reinterpret_cast<uint4*>(sB + 8192 + kb * 2048 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       };
-      if (exact)
-        form(std::integral_constant<int, 2>{});
-      else if (reduce)
-        form(std::integral_constant<int, 1>{});
+      auto form_all = [&](auto att_tag) {
+        if (exact)
+          form(std::integral_constant<int, 2>{}, att_tag);
+        else if (reduce)
+          form(std::integral_constant<int, 1>{}, att_tag);
+        else
+          form(std::integral_constant<int, 0>{}, att_tag);
+      };
+      if (a.axis_att)
+        form_all(std::true_type{});
       else
-        form(std::integral_constant<int, 0>{});
+        form_all(std::false_type{});
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -437,6 +458,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       if (lane == 0) mbar_arrive(&bar_tread);
       grp.advance(ks);
     }
+    if (att_over) dev::set_status(a.status, kStatusNonFinite);
     if (ok && first_flush) {
       // empty chunk: its partials are zero
       const int sub = warp & 3;

@@ -292,6 +292,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
     const int64_t col = col_base + tid;
     const bool row_ok = col < col_end;
     float sb, sc, sbl = 0.f, scl = 0.f;  // sbl, scl: low parts of a double-float s (forward)
+    float att = 0.f;                     // buried object: 2 pi Im(sigma) of the column's beam
+    bool att_over = false;               // an attenuation exponent passed kSepAttMax
     if (a.ntiles) {
       const float4 at = row_ok ? a.atom4[col] : make_float4(0.f, 0.f, 0.f, 0.f);
       sb = at.y;
@@ -300,6 +302,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       const int64_t rb = row_ok ? col / a.n2 : 0, rc = row_ok ? col % a.n2 : 0;
       sb = a.axis_s[a.n0 + rb];
       sc = a.axis_s[a.n0 + a.n1 + rc];
+      if (a.axis_att) att = a.axis_att[rc];
       if (a.axis_lo) {
         sbl = a.axis_lo[a.n0 + rb];
         scl = a.axis_lo[a.n0 + a.n1 + rc];
@@ -343,8 +346,10 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       unsigned char* sB = ringB + bst * kSepBBytes;
       const float4* at = ring_atom[tst];
       // mode 0: raw phase, 1: reduced mod 1, 2: exact products, reduced
-      auto form = [&](auto mode_tag) {
+      // kAtt: a buried object's rows carry exp(-att z')
+      auto form = [&](auto mode_tag, auto att_tag) {
         constexpr int kMode = decltype(mode_tag)::value;
+        constexpr bool kAtt = decltype(att_tag)::value;
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
           uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
@@ -359,6 +364,16 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
                                : fmaf(sb, v.y, fmaf(sc, v.z, v.w));
               float sn, cs;
               dev::sincos_cycles_mufu(ph, &sn, &cs);
+              if (kAtt) {
+                float ex = -att * v.z;
+                if (ex > kSepAttMax) {
+                  ex = kSepAttMax;
+                  att_over = true;
+                }
+                const float gz = __expf(ex);
+                sn *= gz;
+                cs *= gz;
+              }
               split2(cs, sn, hi[q], lo[q]);
             }
           }
@@ -366,12 +381,18 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
           *reinterpret_cast<uint4*>(sB + 16384 + kb * 4096 + b_row_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       };
-      if (exact)
-        form(std::integral_constant<int, 2>{});
-      else if (reduce)
-        form(std::integral_constant<int, 1>{});
+      auto form_all = [&](auto att_tag) {
+        if (exact)
+          form(std::integral_constant<int, 2>{}, att_tag);
+        else if (reduce)
+          form(std::integral_constant<int, 1>{}, att_tag);
+        else
+          form(std::integral_constant<int, 0>{}, att_tag);
+      };
+      if (a.axis_att)
+        form_all(std::true_type{});
       else
-        form(std::integral_constant<int, 0>{});
+        form_all(std::false_type{});
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -421,6 +442,7 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
       if (lane == 0) mbar_arrive(&bar_tfree);
       grp.advance(ks);
     }
+    if (att_over) dev::set_status(a.status, kStatusNonFinite);
     if (ok && first_flush) {
       // empty chunk: its partials are zero
       const int sub = warp & 3;
@@ -473,6 +495,7 @@ __global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ pa
                                                     float inv4a2, const float* __restrict__ axis_s,
                                                     const float* __restrict__ axis_lo, int64_t n0, int64_t n1,
                                                     int64_t n2, float3 H, const double* __restrict__ shift,
+                                                    const float* __restrict__ att, const float* __restrict__ szf,
                                                     int64_t bm_base, float2* out_amp, float* out_int) {
   // the centring shift of the call (integers), once per block
   __shared__ float sh_t[3];
@@ -502,8 +525,10 @@ __global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ pa
       s_hi[u][d] = axis_s[ia[d]];
       s_lo[u][d] = axis_lo[ia[d]];
     }
+    // (a buried object's form factor is taken at the vacuum beam's S_z)
+    const int64_t il = ia[2] - n0 - n1;
     const float S0 = H.x + (s_hi[u][0] + s_lo[u][0]), S1 = H.y + (s_hi[u][1] + s_lo[u][1]),
-                S2 = H.z + (s_hi[u][2] + s_lo[u][2]);
+                S2 = szf ? szf[il] : H.z + (s_hi[u][2] + s_lo[u][2]);
     s2[u] = (S0 * S0 + S1 * S1 + S2 * S2) * inv4a2;
   }
   const int64_t m0 = i0 * ncols + col0;
@@ -546,6 +571,13 @@ __global__ void __launch_bounds__(256) k_sep_reduce(const float* __restrict__ pa
     if (!ok[w]) continue;
     float2 a = v[w];
     if (sh_shifted) a = dev::cmul(dev::shift_phase2(s_hi[w], s_lo[w], sh_t), a);
+    if (att) {
+      // a buried object's attenuation over the centring shift t_z (the rows
+      // carried exp(-2 pi Im(sigma) z') of the centred z')
+      const float g = __expf(-att[(col0 + w) % n2] * sh_t[2]);
+      a.x *= g;
+      a.y *= g;
+    }
     if (out_amp) out_amp[m0 + w] = a;
     if (out_int) out_int[m0 + w] = a.x * a.x + a.y * a.y;
   }
@@ -599,6 +631,9 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
 // The separable grid: the plan's own axes, or for a grazing-incidence plan
 // the virtual grid (h, k, l) whose l axis stacks the four beams' Sz values
 // [Sz1 | Sz2 | -Sz2 | -Sz1] over alpha_f, so each beam is a plain grid sum.
+// A buried object has one beam, l = Re(sigma) per alpha_f; its formed rows
+// carry the attenuation exp(-2 pi Im(sigma) z') and its form factor is taken
+// at the vacuum beam S_1 (the per-column tables sep_att and sep_szf).
 scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   if ((p->s_kind != SCATTER_S_GRID && !gid) || p->batch != 1)
@@ -606,7 +641,17 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   if (p->n_slots % kSepStep) return fail(SCATTER_ERR_UNSUPPORTED, "slot padding is not a multiple of 16");
   std::vector<double> ax64[3];
   for (int d = 0; d < 2; ++d) ax64[d] = p->axis_host[d];
-  if (gid) {
+  const bool buried = gid && p->gid_mode == 1;
+  std::vector<float> att, szf;
+  p->sep_beams = buried ? 1 : 4;
+  if (buried) {
+    const int64_t n_af = p->n_axis[2];
+    ax64[2].assign(p->gid_sz_host.begin(), p->gid_sz_host.begin() + n_af);
+    for (int64_t i = 0; i < n_af; ++i) {
+      att.push_back((float)(6.283185307179586 * p->gid_sz_im_host[i]));
+      szf.push_back((float)p->gid_szf_host[i]);
+    }
+  } else if (gid) {
     const int64_t n_af = p->n_axis[2];
     ax64[2].resize(4 * n_af);
     for (int64_t i = 0; i < n_af; ++i) {
@@ -691,6 +736,14 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
     virt_bytes = (size_t)p->sep_ns * sizeof(float2);
     if ((e = cudaMalloc(&p->d.sep_virt, virt_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc virtual map");
   }
+  if (buried) {
+    const size_t tb = att.size() * sizeof(float);
+    if ((e = cudaMalloc(&p->d.sep_att, tb)) != cudaSuccess) return cuda_status(e, "attenuation table");
+    if ((e = cudaMalloc(&p->d.sep_szf, tb)) != cudaSuccess) return cuda_status(e, "form-factor Sz table");
+    cudaMemcpy(p->d.sep_att, att.data(), tb, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d.sep_szf, szf.data(), tb, cudaMemcpyHostToDevice);
+    virt_bytes += 2 * tb;
+  }
   p->base_bytes += (int64_t)(a_bytes + part_bytes + chunk_bytes + virt_bytes);
   if ((e = sep_prepare_kernel()) != cudaSuccess) return cuda_status(e, "separable shared memory attribute");
   return SCATTER_OK;
@@ -737,6 +790,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.n_mt = p->sep_mt;
   a.partial = p->d.sep_partial;
   a.status = p->d.status;
+  a.axis_att = p->d.sep_att;
   dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)n_chunks);
   timing_begin(p, st);
   const cudaError_t le = sep_launch_core(a, grid, st);
@@ -757,8 +811,8 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
         p->d.sep_partial, sep_part_floats(p->sep_mt, ncols), n_cb, p->d.sep_chunks, n_chunks, p->d.coef, p->d.ftab,
         (float)(1.0 / (4.0 * p->lattice_a * p->lattice_a)), p->d.sep_axis_s, p->d.sep_axis_lo, p->sep_n[0],
         p->sep_n[1], p->sep_n[2],
-        make_float3((float)p->inst[0].H[0], (float)p->inst[0].H[1], (float)p->inst[0].H[2]), p->d.inst_shift, b0,
-        gid ? p->d.sep_virt : amp_out, gid ? nullptr : int_out);
+        make_float3((float)p->inst[0].H[0], (float)p->inst[0].H[1], (float)p->inst[0].H[2]), p->d.inst_shift,
+        p->d.sep_att, p->d.sep_szf, b0, gid ? p->d.sep_virt : amp_out, gid ? nullptr : int_out);
     p->last_launches += 1;
     if (pieces) {
       // h rows 16 b0 .. 16 b1 of the map: a contiguous range of points
