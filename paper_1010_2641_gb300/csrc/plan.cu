@@ -129,9 +129,10 @@ scatter_status validate(const scatter_problem* pr, const scatter_options* op) {
 }
 
 // Error model of the separable path (the relative L2 error of a map whose
-// per-term errors are uncorrelated): tables in FP32 (sincospif, ~2 ulp), f16
-// hi + lo operands with three products (the dropped lo.lo term is below 2^-22
-// of each term), FP32 accumulation in TMEM and in the partials.  `radius`
+// per-term errors are uncorrelated): tables and formed rows from MUFU sin/cos
+// of exactly reduced phases (|error| < 4e-7 = ~7 u each side), f16 hi + lo
+// operands with three products (the dropped lo.lo term is below 2^-22 of
+// each term), FP32 accumulation in TMEM and in the partials.  `radius`
 // bounds |r - t|; *per_pair receives the per-term bound.
 }  // namespace
 
@@ -139,7 +140,7 @@ double separable_error_model(const scatter_plan_s* p, double radius, int split, 
   const double u = std::ldexp(1.0, -24);
   const double pi = 3.14159265358979323846;
   const double sr = (p->s_max[0] + p->s_max[1] + p->s_max[2]) * radius;
-  const double pp = 2.0 * pi * u * (2.0 * sr + 2.0) + 4.0 * std::ldexp(1.0, -22) + 6.0 * u;
+  const double pp = 2.0 * pi * u * (2.0 * sr + 2.0) + 4.0 * std::ldexp(1.0, -22) + 14.0 * u;
   if (per_pair) *per_pair = pp;
   const double steps = (double)std::max<int64_t>(p->n_slots, 1) / 16.0;
   return pp + u * std::sqrt(4096.0 + steps / 256.0 + (double)std::max(split, 1));

@@ -90,7 +90,10 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
     const int64_t slot = ks * kSepStep + kb * 4 + 2 * ri + u;
     float sn = 0.f, cs = 0.f;
     if (a < t.n0) {
-      sincospif(2.0f * (dev::frac_of_product2(sa, sal, t.atom4[slot].x) + sa * t.atom_lo[slot].x), &sn, &cs);
+      // the phase reduced exactly mod 1 (products with their rounding errors
+      // restored), then MUFU sin/cos as for the formed rows: |error| < 4e-7,
+      // below the f16 hi + lo split's resolution
+      dev::sincos_cycles_mufu(dev::frac_of_product2(sa, sal, t.atom4[slot].x) + sa * t.atom_lo[slot].x, &sn, &cs);
       const float w = t.atom_w[slot];
       sn *= w;
       cs *= w;
