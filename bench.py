@@ -510,7 +510,7 @@ def measure_paths(args, dev, clk, only=None):
         inf = plan.info()
         # value from whole calls (every kernel of the call), like the headline's steps
         res["auto_sphere"] = {"value": n_atoms * n_s / (ms_call * 1e-3), "unit": UNIT, "call_ms": ms_call,
-                              "kernel_ms": ms,
+                              "kernel_ms": ms, "l2": "calls back to back, not flushed between them",
                               "path_chosen": {1: "generic", 2: "separable"}.get(inf["path"], str(inf["path"])),
                               "workload": "strained sphere, full map, default options (AUTO, tolerance 1e-4)",
                               "clocks": rc.get("clk")}
