@@ -41,8 +41,10 @@ struct LossArgs {
   const float2* G;        // upstream gradient (vjp mode) or null
   int64_t n_s;
   int grid;
-  const double* S64;
-  const double* axis64;
+  const float* s_hi;       // list: [3][M] offsets s = S - H, FP32
+  const float* s_lo;       //       their rounding errors
+  const float* axis_s;     // grid: [n0 | n1 | n2] offsets, FP32
+  const float* axis_lo;    //       their rounding errors
   int64_t n0, n1, n2;
   double H[3];
   const double* shift;
@@ -57,40 +59,63 @@ struct LossArgs {
   double* loss_part;      // [gridDim.x]
 };
 
+// FP32 arithmetic throughout (GB300 issues FP64 at ~2 operations per SM and
+// clock): S as the plan's double-float offsets s = S - H, the centring phase
+// from them and the integer shift, the misfit d = |A|^2 - I_obs exactly
+// (products with their rounding errors, TwoSum) before its one rounding,
+// and the loss as a double-float sum, folded into FP64 once per thread.
 __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a) {
-  double lpart = 0.0;
-  const double* t = a.shift;
-  const bool shifted = t[0] != 0.0 || t[1] != 0.0 || t[2] != 0.0;
+  __shared__ float sh_t[3];
+  __shared__ int sh_shifted;
+  if (threadIdx.x == 0) {
+    sh_t[0] = (float)a.shift[0];
+    sh_t[1] = (float)a.shift[1];
+    sh_t[2] = (float)a.shift[2];
+    sh_shifted = a.shift[0] != 0.0 || a.shift[1] != 0.0 || a.shift[2] != 0.0;
+  }
+  __syncthreads();
+  const float H0 = (float)a.H[0], H1 = (float)a.H[1], H2 = (float)a.H[2];
+  dev::DFloatSum lsum;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < a.n_s;
        m += (int64_t)gridDim.x * blockDim.x) {
-    double S[3];
+    float s_hi[3], s_lo[3];
     if (a.grid) {
       const int64_t i2 = m % a.n2, line = m / a.n2, i1 = line % a.n1, i0 = line / a.n1;
-      S[0] = a.axis64[i0];
-      S[1] = a.axis64[a.n0 + i1];
-      S[2] = a.axis64[a.n0 + a.n1 + i2];
+      const int64_t ia[3] = {i0, a.n0 + i1, a.n0 + a.n1 + i2};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        s_hi[d] = a.axis_s[ia[d]];
+        s_lo[d] = a.axis_lo[ia[d]];
+      }
     } else {
-      S[0] = a.S64[3 * m];
-      S[1] = a.S64[3 * m + 1];
-      S[2] = a.S64[3 * m + 2];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        s_hi[d] = a.s_hi[d * a.n_s + m];
+        s_lo[d] = a.s_lo[d * a.n_s + m];
+      }
     }
     float2 g;
     if (a.A) {
       const float2 A = a.A[m];
-      const double I = (double)A.x * A.x + (double)A.y * A.y;
-      const double d = I - (double)a.I_obs[m];
-      lpart += d * d;
-      g = make_float2((float)(4.0 * d * A.x), (float)(-4.0 * d * A.y));
+      // d = A.x^2 + A.y^2 - I_obs from the exact products and TwoSums
+      const float p1 = __fmul_rn(A.x, A.x), p2 = __fmul_rn(A.y, A.y);
+      dev::DFloatSum dd;
+      dd.hi = p1;
+      dd.add(p2);
+      dd.add(-a.I_obs[m]);
+      dd.lo = __fadd_rn(dd.lo, __fadd_rn(__fmaf_rn(A.x, A.x, -p1), __fmaf_rn(A.y, A.y, -p2)));
+      const float d = dd.value();
+      lsum.add_product(d, d);
+      g = make_float2(4.f * d * A.x, -4.f * d * A.y);
     } else {
       const float2 G = a.G[m];
       g = make_float2(G.x, -G.y);
     }
-    const float2 ph = shifted ? dev::shift_phase(S[0] - a.H[0], S[1] - a.H[1], S[2] - a.H[2], t)
-                              : make_float2(1.f, 0.f);
+    const float2 ph = sh_shifted ? dev::shift_phase2(s_hi, s_lo, sh_t) : make_float2(1.f, 0.f);
     const float2 gp = dev::cmul(g, ph);
-    const float Sx = (float)S[0], Sy = (float)S[1], Sz = (float)S[2];
+    const float sx = s_hi[0] + s_lo[0], sy = s_hi[1] + s_lo[1], sz = s_hi[2] + s_lo[2];
+    const float Sx = H0 + sx, Sy = H1 + sy, Sz = H2 + sz;
     const float s2 = (Sx * Sx + Sy * Sy + Sz * Sz) * a.inv4a2;
-    const float sx = (float)(S[0] - a.H[0]), sy = (float)(S[1] - a.H[1]), sz = (float)(S[2] - a.H[2]);
     for (int sp = 0; sp < a.n_species; ++sp) {
       const float2 F = a.ftab ? a.ftab[(int64_t)sp * a.n_s + m] : dev::form_factor(a.coef + kNCoef * sp, s2);
       const float2 gF = dev::cmul(gp, F);
@@ -105,6 +130,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_weights(const LossArgs a)
       }
     }
   }
+  double lpart = (double)lsum.hi + (double)lsum.lo;
   // deterministic block reduction of the misfit
   __shared__ double sh[kLossThreads / 32];
   for (int o = 16; o > 0; o >>= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
@@ -640,8 +666,10 @@ scatter_status launch_backward(scatter_plan_t p, const double* xyz, const float*
   la.G = G;
   la.n_s = p->n_s;
   la.grid = p->s_kind == SCATTER_S_GRID;
-  la.S64 = p->d.S64;
-  la.axis64 = p->d.axis64;
+  la.s_hi = p->d.s_hi;
+  la.s_lo = p->d.s_lo;
+  la.axis_s = p->d.axis_s;
+  la.axis_lo = p->d.axis_lo;
   la.n0 = p->n_axis[0];
   la.n1 = p->n_axis[1];
   la.n2 = p->n_axis[2];
