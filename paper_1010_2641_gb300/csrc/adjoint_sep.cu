@@ -138,22 +138,13 @@ struct AdjSepFinalArgs {
   float* grad;             // [n_atoms][3] caller order
 };
 
-// Compensated FP32 accumulator (Neumaier): the running sum and its lost low part.
-struct CompSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ float value() const { return s + c; }
-};
-
 // One thread per atom slot of an N tile: the sum over a (and over the point
-// chunks) with FP32 products and compensated FP32 sums (FP64 runs at ~1/75
-// of the FP32 rate here; the 3 n0 terms are already contracted values whose
-// own error is ~1e-6), then the rotation by e^{2 i pi c} and the H terms in
-// FP64.  Four values of a per iteration keep 24 loads in flight per thread.
+// chunks) with FP32 products and double-float (TwoSum) FP32 sums (FP64 runs
+// at ~1/75 of the FP32 rate here; the 3 n0 terms are already contracted
+// values whose own error is ~1e-6), the row factor e^{2 i pi s_a x'} from
+// MUFU sin/cos of the exactly reduced phase (|error| < 4e-7), then the
+// rotation by e^{2 i pi c} and the H terms in FP64.  Four values of a per
+// iteration keep 24 loads in flight per thread.
 __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f) {
   const Segment t = f.ntiles[blockIdx.x];
   const int64_t slot = t.begin + threadIdx.x;
@@ -163,7 +154,12 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
   const float4 at = f.atom4[slot];
   const int64_t rows = 3 * f.n0;
   const int* se = f.sexp + (int64_t)t.species * rows;
-  CompSum V[2], Wd[3][2];
+  dev::DFloatSum V[2], Wd[3][2];
+  // the partials' offset of D entry (m, slot) is the column's part plus the
+  // row's (sep_part_off): the column part once per thread, and rows 2 r and
+  // 2 r + 1 (Re, Im) are neighbours in the same 32-row block, 4 floats apart
+  const int64_t col_off = sep_part_off(0, slot, f.n_cb);
+  const int64_t row_block = f.n_cb << 10;  // floats per 32-row block
   constexpr int kU = 4;
   for (int64_t a0 = 0; a0 < f.n0; a0 += kU) {
     float U[kU][3][2];
@@ -174,11 +170,11 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
         U[u][w][0] = U[u][w][1] = 0.f;
         const int64_t a = a0 + u;
         if (a < f.n0) {
-          const int64_t row = w * f.n0 + a;
-          for (int c = 0; c < f.n_chunks; ++c) {
-            const float* pc = f.partial + (int64_t)c * f.chunk_floats;
-            U[u][w][0] += pc[sep_part_off(2 * row, slot, f.n_cb)];
-            U[u][w][1] += pc[sep_part_off(2 * row + 1, slot, f.n_cb)];
+          const int64_t m = 2 * (w * f.n0 + a);
+          const float* pc = f.partial + col_off + (m >> 5) * row_block + ((m & 31) << 2);
+          for (int c = 0; c < f.n_chunks; ++c, pc += f.chunk_floats) {
+            U[u][w][0] += pc[0];
+            U[u][w][1] += pc[4];
           }
         }
       }
@@ -188,7 +184,7 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
       if (a >= f.n0) break;
       const float sa = f.axis_s[a];
       float sn, cs;
-      sincospif(2.0f * dev::frac_of_product(sa, at.x), &sn, &cs);
+      dev::sincos_cycles_mufu(dev::frac_of_product(sa, at.x), &sn, &cs);
       float P[3][2];
 #pragma unroll
       for (int w = 0; w < 3; ++w) {
@@ -210,10 +206,11 @@ __global__ void __launch_bounds__(kSepN) k_adj_sep_final(const AdjSepFinalArgs f
   double sn, cs;
   sincospi(2.0 * (double)at.w, &sn, &cs);
   const double scale = -2.0 * 3.14159265358979323846 * (double)f.atom_w[slot];
-  const double vr = V[0].value(), vi = V[1].value();
+  auto dval = [](const dev::DFloatSum& q) { return (double)q.hi + (double)q.lo; };
+  const double vr = dval(V[0]), vi = dval(V[1]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double xr = f.H[d] * vr + Wd[d][0].value(), xi = f.H[d] * vi + Wd[d][1].value();
+    const double xr = f.H[d] * vr + dval(Wd[d][0]), xi = f.H[d] * vi + dval(Wd[d][1]);
     f.grad[3 * (int64_t)src + d] = (float)(scale * (cs * xi + sn * xr));  // Im(e^{2 i pi c} X)
   }
 }
