@@ -373,10 +373,10 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adjoint(const AdjArgs a) {
 // gF.im).  Along the line the phase advances by ds z'_j per point, so
 // e^{2 i pi phi} is carried from point to point by one complex multiply
 // with w_j = e^{2 i pi ds z'_j} instead of a MUFU sin/cos per pair (four
-// FMA-pipe ops; the pair costs eight in all, no MUFU).  Every 64 points the
+// FMA-pipe ops; the pair costs eight in all, no MUFU).  Every 128 points the
 // exponential is re-seeded from the exactly reduced phase, which bounds the
-// rounding drift of the recurrence to ~64 products (~1e-5 relative, against
-// the 1e-3 tolerance of the gradients).  Per tile: FP32 line sums
+// rounding drift of the recurrence to ~128 products with w accurate to ~1
+// ulp (~1e-5 relative, against the 1e-3 tolerance of the gradients).  Per tile: FP32 line sums
 // sum v and sum S_z v, folded into double-float outer sums (FP32 pairs on
 // the FMA pipe) as S_x sum v, S_y sum v, sum S_z v.
 struct AdjLineArgs {
@@ -393,7 +393,7 @@ struct AdjLineArgs {
   unsigned* status;
 };
 
-constexpr int kReseed = 64;  // points between exact re-seeds of the recurrence
+constexpr int kReseed = 128;  // points between exact re-seeds of the recurrence
 
 __global__ void __launch_bounds__(kAdjThreads, 4) k_adjoint_line(const AdjLineArgs a) {
   __shared__ __align__(128) float4 sh_s[2][kSTile];
@@ -417,7 +417,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adjoint_line(const AdjLineAr
     z[r] = at.z;
     c[r] = at.w;
     float sn, cs;
-    dev::sincos_cycles_mufu(dev::frac_of_product(a.ds, z[r]), &sn, &cs);  // rotation per l step
+    // rotation per l step, accurate to ~1 ulp (its error compounds along
+    // the line between re-seeds)
+    sincospif(2.0f * dev::frac_of_product(a.ds, z[r]), &sn, &cs);
     wr[r] = cs;
     wi[r] = sn;
   }
