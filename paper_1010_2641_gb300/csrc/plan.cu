@@ -164,9 +164,21 @@ bool auto_prefers_separable(const scatter_plan_s* p, const scatter_options* op) 
   const int64_t n0 = p->n_axis[0];
   const int64_t n12 = p->n_axis[1] * (p->s_kind == SCATTER_S_GID_GRID ? 4 * p->n_axis[2] : p->n_axis[2]);
   // B rows are formed once per 16 atoms for 2 x 64 values of the first axis:
-  // with fewer than 16 of them, or less than four 256-point column tiles, or
-  // a few hundred steps of atoms, the formation and the fixed costs dominate
-  if (n0 < 16 || n12 < 1024 || p->n_slots < 4096) return false;
+  // with fewer than 16 of them, or a few hundred steps of atoms, the
+  // formation and the fixed costs dominate
+  if (n0 < 16 || p->n_slots < 4096) return false;
+  if (n12 < 1024) {
+    // less than four 256-point column tiles: only for a large sum, when the
+    // contraction (three f16 products on padded 256 x 256 tiles at ~2e15
+    // flop/s) and its per-call table (8 B per row and atom slot at ~5e12 B/s)
+    // come out at least twice as fast as the generic kernel (~2.3e12 pairs/s)
+    const double pairs = (double)p->n_atoms * (double)n0 * (double)n12;
+    if (pairs < 1e10) return false;
+    const double rows = std::ceil(2.0 * (double)n0 / 256.0) * 256.0, cols = std::ceil((double)n12 / 256.0) * 256.0;
+    const double slots = (double)p->n_slots;
+    const double sep_s = 6.0 * rows * cols * 2.0 * slots / 2.0e15 + rows * slots * 8.0 / 5.0e12 + 3.0e-5;
+    if (2.0 * sep_s > pairs / 2.3e12) return false;
+  }
   const double tol = op && op->tolerance > 0.0 ? op->tolerance : 1e-4;
   const double radius = op && op->radius_hint > 0.0
                             ? op->radius_hint

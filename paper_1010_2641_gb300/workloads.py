@@ -94,6 +94,25 @@ def simple_cubic(n=(10, 10, 10), origin=(0, 0, 0)) -> np.ndarray:
     return xyz + np.asarray(origin, dtype=np.float64)
 
 
+def example_cube_100(strained: bool = False) -> np.ndarray:
+    """The first worked example of Section 4: a simple cubic crystal of
+    100 x 100 x 100 cells, one atom per cell at x, y in [-50, 50), z in
+    [0, 100) (lattice units, f = 1).  strained=True adds the displacement
+    field of the same example along z, u_z = 1e-6 z (x^2 + y^2) (at most
+    ~0.5 cells at the corners).  1,000,000 atoms."""
+    xyz = simple_cubic((100, 100, 100), origin=(-50, -50, 0))
+    if strained:
+        xyz[:, 2] += 1e-6 * xyz[:, 2] * (xyz[:, 0] ** 2 + xyz[:, 1] ** 2)
+    return xyz
+
+
+def example_cube_axes():
+    """Its map around (004): h = -0.1 ... 0.099 and l = 3.9 ... 4.099 in steps
+    of 0.001 (200 values each), k = 0: a 200 x 1 x 200 grid (40,000 points)."""
+    i = np.arange(200, dtype=np.float64)
+    return [-0.1 + 0.001 * i, np.zeros(1), 3.9 + 0.001 * i]
+
+
 def linear_chain(n: int, sigma: float = 0.0, seed: int = 0) -> np.ndarray:
     """Atoms at x = 0..n-1 (Section 2.3), optionally with Gaussian noise of std sigma."""
     xyz = np.zeros((n, 3))
