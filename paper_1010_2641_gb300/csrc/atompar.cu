@@ -44,6 +44,7 @@ struct ApArgs {
   const double* shift;             // [3] the call's centring t
   float smax[3];                   // max |S_d - H_d| over the points
   float2* partial;        // [block][M]
+  int tile;               // reflections per CTA (<= kApPts)
 };
 
 // EXACT: the phase with its products' rounding errors restored and s and the
@@ -142,8 +143,8 @@ __global__ void __launch_bounds__(kApThreads, 2) k_atompar(const ApArgs a) {
   __shared__ float2 sh_part[kApWarps][kApPts];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Segment blk = a.blocks[blockIdx.y];
-  const int64_t p0 = (int64_t)blockIdx.x * kApPts;
-  const int np = (int)dev::min64(kApPts, a.n_s - p0);
+  const int64_t p0 = (int64_t)blockIdx.x * a.tile;
+  const int np = (int)dev::min64(a.tile, a.n_s - p0);
 
   // the tile's S offsets s = S - H
   for (int i = tid; i < np; i += kApThreads) {
@@ -229,6 +230,32 @@ std::vector<Segment> atompar_blocks(const scatter_plan_s* p, int K) {
 
 }  // namespace
 
+// Reflections per CTA.  Every CTA of a block costs the same (each thread
+// runs all K of its atoms), so the call lasts ceil(CTAs / resident CTAs)
+// waves of one CTA's time, which scales with its reflections plus a fixed
+// part (its atoms' loads, the tile's S offsets, the block sums).  The tile
+// that minimises that product fills the last wave: for 245 blocks x 1000
+// reflections on 304 resident CTAs, 11 tiles of 91 (9 waves) instead of 8
+// of 125 (7 waves, the last under half full).
+int atompar_tile(int64_t n_s, int64_t n_blocks, int64_t resident) {
+  if (n_s <= 0 || n_blocks <= 0 || resident <= 0) return kApPts;
+  constexpr double kFixed = 6.0;  // the fixed part, in reflections
+  const int64_t t_min = (n_s + kApPts - 1) / kApPts;
+  double best = 1e300;
+  int best_tile = kApPts;
+  for (int64_t t = t_min; t <= 4 * t_min; ++t) {
+    const int64_t tile = (n_s + t - 1) / t;
+    const int64_t tiles = (n_s + tile - 1) / tile;
+    const double waves = (double)((tiles * n_blocks + resident - 1) / resident);
+    const double cost = waves * ((double)tile + kFixed);
+    if (cost < best * 0.999) {
+      best = cost;
+      best_tile = (int)tile;
+    }
+  }
+  return best_tile;
+}
+
 bool atompar_applicable(const scatter_plan_s* p) {
   return p->batch == 1 && (p->s_kind == SCATTER_S_LIST || p->s_kind == SCATTER_S_GRID) && p->n_s > 0;
 }
@@ -277,6 +304,10 @@ scatter_status prepare_atompar(scatter_plan_s* p, int K) {
   p->tiling_bytes += (int64_t)(blocks.size() * sizeof(Segment) + part * sizeof(float2));
   p->ap_n_blocks = (int32_t)blocks.size();
   p->tiling.atom_k = K;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_atompar(K), kApThreads, 0)) != cudaSuccess)
+    return cuda_status(e, "atom-parallel occupancy");
+  p->ap_tile = atompar_tile(p->n_s, (int64_t)blocks.size(), (int64_t)std::max(per_sm, 1) * p->n_sm);
   return SCATTER_OK;
 }
 
@@ -305,7 +336,8 @@ scatter_status launch_atompar(scatter_plan_t p, float2* amp_out, float* int_out,
   a.shift = p->d.inst_shift;
   for (int d = 0; d < 3; ++d) a.smax[d] = (float)p->s_max[d];
   a.partial = p->d.partial;
-  dim3 grid((unsigned)((p->n_s + kApPts - 1) / kApPts), (unsigned)p->ap_n_blocks);
+  a.tile = p->ap_tile > 0 ? p->ap_tile : kApPts;
+  dim3 grid((unsigned)((p->n_s + a.tile - 1) / a.tile), (unsigned)p->ap_n_blocks);
   void* args[] = {&a};
   timing_begin(p, st);
   cudaError_t e = cudaLaunchKernel(fn, grid, dim3(kApThreads), args, 0, st);

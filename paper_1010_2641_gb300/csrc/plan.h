@@ -209,6 +209,7 @@ struct scatter_plan_s {
   int32_t sep_n_chunks = 0;
   float sep_smax[2] = {0.f, 0.f};               // max |s| of the separable grid's b and c axes
   int32_t ap_n_blocks = 0;
+  int32_t ap_tile = 0;               // reflections per atom-parallel CTA (<= kApPts)
   std::vector<double> gid_sz_host;               // [2][n_af] Sz1, Sz2 (r.l.u.)
   std::vector<double> gid_sz_im_host;            // [n_af] Im sigma of a buried object's beam
   std::vector<double> gid_szf_host;              // [4][n_af] S_z of each beam's form factor
