@@ -383,7 +383,7 @@ scatter_status launch_adjoint_sep(scatter_plan_t p, float* grad, cudaStream_t st
   for (int d = 0; d < 3; ++d) f.H[d] = p->inst[0].H[d];
   f.grad = grad;
   k_adj_sep_final<<<(unsigned)p->adj_sep_ntiles, kSepN, 0, st>>>(f);
-  p->last_launches += 4;
+  p->last_launches += 3 + sep_core_launches(p->adj_sep_mt);
   return cuda_status(cudaGetLastError(), "adjoint launch");
 }
 

@@ -112,6 +112,8 @@ struct SepArgs {
   unsigned* status;
   const float* axis_att;  // forward of a buried object: per l, 2 pi Im(sigma); the formed
                           // rows carry exp(-axis_att[l] z'); null otherwise
+  int64_t mp_first;       // M-tile pairs of this launch: [mp_first, mp_first + mp_count)
+  int64_t mp_count;       // (0: all (n_mt + 1) / 2 of them)
 };
 
 // Partials in the accumulator's own blocking.  D row m (TMEM lane of its M
@@ -144,6 +146,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Launches k_sep on `st` (its shared-memory attribute set by sep_prepare_kernel).
 cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st);
+// kernels sep_launch_core launches for n_mt M tiles (1, or 2 when an odd
+// M-tile pair count splits between the CTA-pair and the one-CTA kernel)
+int sep_core_launches(int64_t n_mt);
 cudaError_t sep_prepare_kernel();
 // The CTA-pair form (sep_pair.cu): n_nt N tiles, n_chunks atom chunks.
 cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);

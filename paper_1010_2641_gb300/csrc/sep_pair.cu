@@ -149,11 +149,12 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool mma_warp = warp == kSepFormWarps, copy_warp = warp == kSepFormWarps + 1;
   const uint32_t rank = cluster_rank();
-  const int64_t n_mp = (a.n_mt + 1) / 2;     // M-tile pairs
+  const int64_t n_mp = a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2;  // M-tile pairs of this launch
   const int64_t n_mq = (n_mp + 1) / 2;       // M quads (one per cluster)
   const int64_t cl = blockIdx.x >> 1;
   const int64_t mq = cl % n_mq, nt = cl / n_mq;
   const int ntp = 2 * mq + 1 < n_mp ? 2 : 1;  // tile pairs of this quad with rows
+  const int64_t mp0 = a.mp_first + 2 * mq;   // the quad's first M-tile pair
   const int chunk = blockIdx.y;
   const int64_t nbc = a.n1 * a.n2;
   int64_t col_base = nt * kSepN, col_end = nbc;
@@ -226,7 +227,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         dev::mbar_arrive_expect_tx(&bar_ready[ast], (uint32_t)ntp * kPairTileBytes);
         for (int tp = 0; tp < ntp; ++tp)
           dev::bulk_g2s(ringA + (ast * 2 + tp) * kPairTileBytes,
-                        Abase + (2 * mq + tp) * pair_stride + ks * (kSepPair * kSepABytes / 16), kPairTileBytes,
+                        Abase + (mp0 + tp) * pair_stride + ks * (kSepPair * kSepABytes / 16), kPairTileBytes,
                         &bar_ready[ast]);
         a_issued = g + 1;
       }
@@ -430,7 +431,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m0 = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32;
+        const int64_t m0 = (2 * (mp0 + tp) + rank) * kSepM + sub * 32;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
           const int64_t bc0 = col_base + col0 + cc;
@@ -464,7 +465,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
       const int sub = warp & 3;
       const int col0 = (warp >> 2) * 128;
       for (int tp = 0; tp < ntp; ++tp) {
-        const int64_t m0 = (2 * (2 * mq + tp) + rank) * kSepM + sub * 32;
+        const int64_t m0 = (2 * (mp0 + tp) + rank) * kSepM + sub * 32;
         for (int cc = 0; cc < 128 && col_base + col0 + cc < col_end; cc += 32) {
           float4* blk = reinterpret_cast<float4*>(part + sep_part_off(m0, col_base + col0 + cc, a.n_cb)) + lane;
           for (int q = 0; q < 8; ++q) blk[q * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -508,7 +509,7 @@ cudaError_t sep_pair_prepare_kernel() {
 
 // Grid: x = 2 CTAs x M quads x N tiles (cluster pairs along x), y = chunks.
 cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st) {
-  const int64_t n_mq = ((a.n_mt + 1) / 2 + 1) / 2;
+  const int64_t n_mq = ((a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2) + 1) / 2;
   dim3 grid((unsigned)(2 * n_mq * n_nt), (unsigned)n_chunks);
   k_sep_pair<<<grid, kSepThreads, kPairSmem, st>>>(a);
   return cudaGetLastError();

@@ -159,8 +159,8 @@ __global__ void __maxnreg__(168) k_sep(const SepArgs a) {
   unsigned char* ringB = smem + kSepAStages * kSepPair * kSepABytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool mma_warp = warp == kSepFormWarps, copy_warp = warp == kSepFormWarps + 1;
-  const int64_t n_mp = (a.n_mt + 1) / 2;
-  const int64_t mp = blockIdx.x % n_mp, nt = blockIdx.x / n_mp;
+  const int64_t n_mp = a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2;  // pairs of this launch
+  const int64_t mp = a.mp_first + blockIdx.x % n_mp, nt = blockIdx.x / n_mp;
   const int ntp = 2 * mp + 1 < a.n_mt ? 2 : 1;  // M tiles of this CTA with rows
   const int chunk = blockIdx.y;
   const int64_t nbc = a.n1 * a.n2;
@@ -597,15 +597,32 @@ cudaError_t sep_prepare_kernel() {
 }
 
 // grid: x = M-tile pairs x N tiles, y = chunks.  The CTA-pair kernel
-// (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster; with
-// an odd number of pairs one cluster per N tile would run one accumulator
-// tile against a full B formation, so those grids keep the one-CTA kernel.
+// (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster.  An
+// odd last pair runs on the one-CTA kernel after it: a pair cluster with one
+// accumulator tile would form all of its B columns for half the MMA work.
 cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
   const int64_t n_mp = (a.n_mt + 1) / 2;
-  if (sep_pair_enabled() && n_mp % 2 == 0)
-    return sep_pair_launch_core(a, (int64_t)grid.x / n_mp, (int)grid.y, st);
-  k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
+  const int64_t n_nt = (int64_t)grid.x / n_mp;
+  const int64_t n_even = n_mp & ~int64_t(1);
+  if (!sep_pair_enabled() || n_even == 0) {
+    k_sep<<<grid, kSepThreads, kSepSmem, st>>>(a);
+    return cudaGetLastError();
+  }
+  SepArgs pa = a;
+  pa.mp_first = 0;
+  pa.mp_count = n_even;
+  cudaError_t e = sep_pair_launch_core(pa, n_nt, (int)grid.y, st);
+  if (e != cudaSuccess || n_even == n_mp) return e;
+  SepArgs sa = a;
+  sa.mp_first = n_even;
+  sa.mp_count = 1;
+  k_sep<<<dim3((unsigned)n_nt, grid.y), kSepThreads, kSepSmem, st>>>(sa);
   return cudaGetLastError();
+}
+
+int sep_core_launches(int64_t n_mt) {
+  const int64_t n_mp = (n_mt + 1) / 2;
+  return (sep_pair_enabled() && n_mp >= 2 && n_mp % 2 == 1) ? 2 : 1;
 }
 
 namespace {
@@ -799,7 +816,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   const cudaError_t le = sep_launch_core(a, grid, st);
   timing_end(p, st);
   if (le != cudaSuccess) return cuda_status(le, "separable kernel launch");
-  p->last_launches += 1;
+  p->last_launches += sep_core_launches(p->sep_mt);
   const bool gid = p->s_kind == SCATTER_S_GID_GRID;
   const int64_t n_cb = (p->sep_n[1] * p->sep_n[2] + 31) / 32;
   const int64_t n_bm = (2 * p->sep_n[0] + 31) / 32;  // 32-row blocks holding map rows

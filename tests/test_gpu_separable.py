@@ -42,8 +42,13 @@ def test_tiny_cube_dirichlet():
     assert rel_l2(A, oracle.amplitude(xyz, S, W.unit_species()[None], A_LAT)) < TOL_TC
 
 
+# n0 sets the M tiles (2 n0 rows of 128): 130 -> 3 tiles in 2 pairs (the
+# CTA-pair kernel with a zero padding tile), 200 -> 2 full pairs, 300 -> 5
+# tiles in 3 pairs and 384 -> 3 full pairs (two on the CTA-pair kernel, the
+# last on the one-CTA kernel), 520 -> 9 tiles in 5 pairs
 @pytest.mark.parametrize("shape,split", [((16, 16, 64), 0), ((5, 7, 13), 0), ((70, 3, 37), 2), ((1, 1, 1), 0),
-                                         ((33, 9, 30), 5)])
+                                         ((33, 9, 30), 5), ((130, 5, 11), 0), ((200, 4, 9), 3),
+                                         ((300, 3, 7), 0), ((384, 2, 9), 2), ((520, 2, 5), 0)])
 def test_sphere_grids(shape, split):
     c = W.fcc_sphere(radius_cells=4.3, seed=9)
     occ = np.random.default_rng(3).uniform(0.5, 1.0, len(c.xyz)).astype(np.float32)
