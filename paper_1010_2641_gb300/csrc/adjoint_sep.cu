@@ -308,6 +308,7 @@ scatter_status prepare_adjoint_sep(scatter_plan_s* p) {
           cudaSuccess)
     return cuda_status(e, "adjoint tables upload");
   if ((e = sep_prepare_kernel()) != cudaSuccess) return cuda_status(e, "separable shared memory attribute");
+  if (const scatter_status ss = sep_prepare_side(p, n_mt); ss != SCATTER_OK) return ss;
   p->base_bytes += (int64_t)(gf_bytes + sexp_bytes + a_bytes + part_bytes + rec.size() * sizeof(float4) +
                              (ntiles.size() + chunks.size()) * sizeof(Segment));
   p->adj_sep_ksteps = n_ksteps;
@@ -364,7 +365,7 @@ scatter_status launch_adjoint_sep(scatter_plan_t p, float* grad, cudaStream_t st
   a.status = p->d.status;
   dim3 grid((unsigned)(n_mp * p->adj_sep_ntiles), (unsigned)p->adj_sep_chunks);
   timing_begin(p, st);
-  const cudaError_t le = sep_launch_core(a, grid, st);
+  const cudaError_t le = sep_launch_core(a, grid, st, p->side_stream, p->side_fork, p->side_join);
   timing_end(p, st);
   if (le != cudaSuccess) return cuda_status(le, "adjoint contraction launch");
   AdjSepFinalArgs f{};

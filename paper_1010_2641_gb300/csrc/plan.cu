@@ -346,6 +346,9 @@ extern "C" void scatter_plan_destroy(scatter_plan_t p) {
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   for (cudaEvent_t& e : p->copy_ev)
     if (e) cudaEventDestroy(e);
+  if (p->side_stream) cudaStreamDestroy(p->side_stream);
+  if (p->side_fork) cudaEventDestroy(p->side_fork);
+  if (p->side_join) cudaEventDestroy(p->side_join);
   if (prev >= 0) cudaSetDevice(prev);
   delete p;
 }

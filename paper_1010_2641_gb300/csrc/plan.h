@@ -231,4 +231,8 @@ struct scatter_plan_s {
   void* host_out = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ev[scatter::kHostPieces + 1] = {};
+  // separable contractions with an odd M-tile pair count of 3 or more: the
+  // last pair's one-CTA kernel runs on side_stream beside the CTA-pair kernel
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
 };

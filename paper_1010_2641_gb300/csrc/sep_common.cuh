@@ -145,10 +145,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Launches k_sep on `st` (its shared-memory attribute set by sep_prepare_kernel).
-cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st);
+// side, fork, join: where an odd M-tile pair count splits between the two
+// kernels, the one-CTA kernel's launch runs on `side`, forked from `st` by
+// `fork` and joined back by `join`, beside the CTA-pair kernel (null: after
+// it on `st`)
+cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st, cudaStream_t side = nullptr,
+                            cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 // kernels sep_launch_core launches for n_mt M tiles (1, or 2 when an odd
 // M-tile pair count splits between the CTA-pair and the one-CTA kernel)
 int sep_core_launches(int64_t n_mt);
+// creates the plan's side stream and its events where n_mt M tiles split
+scatter_status sep_prepare_side(scatter_plan_s* p, int64_t n_mt);
 cudaError_t sep_prepare_kernel();
 // The CTA-pair form (sep_pair.cu): n_nt N tiles, n_chunks atom chunks.
 cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st);

@@ -598,9 +598,12 @@ cudaError_t sep_prepare_kernel() {
 
 // grid: x = M-tile pairs x N tiles, y = chunks.  The CTA-pair kernel
 // (sep_pair.cu) covers the same tiles with two M-tile pairs per cluster.  An
-// odd last pair runs on the one-CTA kernel after it: a pair cluster with one
-// accumulator tile would form all of its B columns for half the MMA work.
-cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
+// odd last pair runs on the one-CTA kernel (a pair cluster with one
+// accumulator tile would form all of its B columns for half the MMA work),
+// on the side stream where one is given, so that its CTAs take the SMs the
+// pair kernel's last clusters leave idle.
+cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
+                            cudaEvent_t join) {
   const int64_t n_mp = (a.n_mt + 1) / 2;
   const int64_t n_nt = (int64_t)grid.x / n_mp;
   const int64_t n_even = n_mp & ~int64_t(1);
@@ -611,13 +614,38 @@ cudaError_t sep_launch_core(const SepArgs& a, dim3 grid, cudaStream_t st) {
   SepArgs pa = a;
   pa.mp_first = 0;
   pa.mp_count = n_even;
-  cudaError_t e = sep_pair_launch_core(pa, n_nt, (int)grid.y, st);
-  if (e != cudaSuccess || n_even == n_mp) return e;
   SepArgs sa = a;
   sa.mp_first = n_even;
   sa.mp_count = 1;
-  k_sep<<<dim3((unsigned)n_nt, grid.y), kSepThreads, kSepSmem, st>>>(sa);
-  return cudaGetLastError();
+  const bool split = n_even < n_mp;
+  const bool beside = split && side && fork && join;
+  cudaError_t e = cudaSuccess;
+  if (beside && ((e = cudaEventRecord(fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess))
+    return e;
+  e = sep_pair_launch_core(pa, n_nt, (int)grid.y, st);
+  if (split) {
+    if (e == cudaSuccess) {
+      k_sep<<<dim3((unsigned)n_nt, grid.y), kSepThreads, kSepSmem, beside ? side : st>>>(sa);
+      e = cudaGetLastError();
+    }
+    if (beside) {  // join even after a failed launch: a capture needs the side stream back
+      const cudaError_t ej = cudaEventRecord(join, side);
+      const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(st, join, 0) : ej;
+      if (e == cudaSuccess) e = ew;
+    }
+  }
+  return e;
+}
+
+scatter_status sep_prepare_side(scatter_plan_s* p, int64_t n_mt) {
+  if (sep_core_launches(n_mt) < 2 || p->side_stream) return SCATTER_OK;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_status(e, "side stream");
+  if ((e = cudaEventCreateWithFlags(&p->side_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&p->side_join, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_status(e, "side stream events");
+  return SCATTER_OK;
 }
 
 int sep_core_launches(int64_t n_mt) {
@@ -766,7 +794,7 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   }
   p->base_bytes += (int64_t)(a_bytes + part_bytes + chunk_bytes + virt_bytes);
   if ((e = sep_prepare_kernel()) != cudaSuccess) return cuda_status(e, "separable shared memory attribute");
-  return SCATTER_OK;
+  return sep_prepare_side(p, n_mt);
 }
 
 scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_out, cudaStream_t st) {
@@ -813,7 +841,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.axis_att = p->d.sep_att;
   dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)n_chunks);
   timing_begin(p, st);
-  const cudaError_t le = sep_launch_core(a, grid, st);
+  const cudaError_t le = sep_launch_core(a, grid, st, p->side_stream, p->side_fork, p->side_join);
   timing_end(p, st);
   if (le != cudaSuccess) return cuda_status(le, "separable kernel launch");
   p->last_launches += sep_core_launches(p->sep_mt);
