@@ -207,6 +207,7 @@ struct scatter_plan_s {
   int64_t sep_n[3] = {0, 0, 0};                  // separable grid shape (GID: n_h, n_k, 4 n_af)
   int64_t sep_ns = 0;
   int32_t sep_n_chunks = 0;
+  bool sep_form_a = false;                       // A formed inside the CTA-pair kernel, no A table
   float sep_smax[2] = {0.f, 0.f};               // max |s| of the separable grid's b and c axes
   int32_t ap_n_blocks = 0;
   int32_t ap_tile = 0;               // reflections per atom-parallel CTA (<= kApPts)

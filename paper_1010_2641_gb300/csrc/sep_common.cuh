@@ -114,6 +114,10 @@ struct SepArgs {
                           // rows carry exp(-axis_att[l] z'); null otherwise
   int64_t mp_first;       // M-tile pairs of this launch: [mp_first, mp_first + mp_count)
   int64_t mp_count;       // (0: all (n_mt + 1) / 2 of them)
+  int form_a;             // CTA-pair forward: 1 = the A tiles are formed in the kernel from the
+                          // records (rec_lo, rec_w beside them) instead of streamed from `A`
+  const float4* rec_lo;   //   the records' position rounding errors (x' error read)
+  const float* rec_w;     //   the atoms' occupancies
 };
 
 // Partials in the accumulator's own blocking.  D row m (TMEM lane of its M

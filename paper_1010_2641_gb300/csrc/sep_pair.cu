@@ -131,6 +131,11 @@ __device__ __forceinline__ void commit_pair(uint64_t* bar) {
 //   bar_tempty[t] atom records read by this CTA's formation     (8 warps)
 //   bar_tread     this CTA's accumulators read out              (8 warps)
 //   bar_pfree     rank 0: rank 1's accumulators read out        (relay)
+// FORM_A: the formation warps also form this CTA's A tiles from the step's
+// atom records (with their x' errors and occupancies) instead of the copy
+// warp streaming them from the table (a grid of one N tile, where the table
+// would be written and read once).
+template <bool FORM_A>
 __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepArgs a) {
   extern __shared__ __align__(1024) unsigned char pair_smem_raw[];
   __shared__ __align__(8) uint64_t bar_ready[kPairAStages];
@@ -140,6 +145,9 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   __shared__ __align__(8) uint64_t bar_tread;
   __shared__ __align__(8) uint64_t bar_pfree;
   __shared__ __align__(16) float4 ring_atom[kPairTStages][kSepStep];
+  // FORM_A: the records' x' errors and occupancies (one unused stage otherwise)
+  __shared__ __align__(16) float4 ring_lo[FORM_A ? kPairTStages : 1][kSepStep];
+  __shared__ __align__(16) float ring_w[FORM_A ? kPairTStages : 1][kSepStep];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -175,7 +183,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   }
   if (tid == 0) {
     for (int s = 0; s < kPairAStages; ++s) {
-      dev::mbar_init(&bar_ready[s], 1 + kSepFormWarps + (rank == 0 ? 1 : 0));
+      dev::mbar_init(&bar_ready[s], (FORM_A ? 0 : 1) + kSepFormWarps + (rank == 0 ? 1 : 0));
       dev::mbar_init(&bar_done[s], 1);
     }
     for (int s = 0; s < kPairTStages; ++s) {
@@ -215,6 +223,16 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
             !dev::mbar_wait_bounded(&bar_tempty[tst], (uint32_t)(((g - kPairTStages) / kPairTStages) & 1))) {
           ok = false;
           break;
+        }
+        if constexpr (FORM_A) {
+          // the records, their x' errors and occupancies: the formation warps
+          // build the step's A tiles from them
+          dev::mbar_arrive_expect_tx(&bar_atom[tst], kSepStep * (2 * sizeof(float4) + sizeof(float)));
+          dev::bulk_g2s(&ring_atom[tst][0], a.rec + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
+          dev::bulk_g2s(&ring_lo[tst][0], a.rec_lo + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
+          dev::bulk_g2s(&ring_w[tst][0], a.rec_w + ks * kSepStep, kSepStep * sizeof(float), &bar_atom[tst]);
+          t_issued = g + 1;
+          continue;
         }
         dev::mbar_arrive_expect_tx(&bar_atom[tst], kSepStep * sizeof(float4));
         dev::bulk_g2s(&ring_atom[tst][0], a.rec + ks * kSepStep, kSepStep * sizeof(float4), &bar_atom[tst]);
@@ -345,6 +363,22 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         exact = bound > dev::kPhaseExactLim;
       }
     }
+    // FORM_A: this thread's four 16-byte rows of the step's A tiles (the
+    // table kernel's units: 4 atoms of one row m in one K block), unit
+    // i * 256 + tid of the CTA's 2 x 512; m = 2 a + {Re, Im}, and the two
+    // lanes of a row pair share X = w e^{2 pi i s_a x'} of their 4 atoms
+    constexpr int kAUnits = FORM_A ? 4 : 1;
+    float a_s[kAUnits], a_sl[kAUnits];
+    bool a_ok[kAUnits];
+#pragma unroll
+    for (int i = 0; i < kAUnits; ++i) {
+      const int unit = i * 256 + tid, tp = unit >> 9, u = unit & 511;
+      const int64_t m = (int64_t)(2 * (mp0 + tp) + (int)rank) * kSepM + ((u >> 3) & 15) * 8 + (u & 7);
+      const int64_t ah = m >> 1;
+      a_ok[i] = FORM_A && tp < ntp && ah < a.n0;
+      a_s[i] = a_ok[i] ? a.axis_s[ah] : 0.f;
+      a_sl[i] = a_ok[i] ? a.axis_lo[ah] : 0.f;
+    }
     float* part = a.partial + (int64_t)chunk * a.chunk_floats;
     bool first_flush = true;
     int64_t g = 0;
@@ -411,6 +445,53 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         form_all(std::true_type{});
       else
         form_all(std::false_type{});
+      if constexpr (FORM_A) {
+        // the step's A tiles of this CTA (rows of M tile 2 (mp0 + tp) + rank
+        // of every tile pair with rows), as the table kernel writes them: the phase
+        // s_a x' with its products' rounding errors restored, MUFU sin/cos,
+        // the occupancy, rows Re (Xr, -Xi) and Im (Xi, Xr), f16 hi and lo
+        const float4* atl = ring_lo[tst];
+        const float* atw = ring_w[tst];
+#pragma unroll
+        for (int i = 0; i < kAUnits; ++i) {
+          const int unit = i * 256 + tid, tp = unit >> 9, u = unit & 511;
+          if (tp >= ntp) continue;  // the same for the whole warp
+          const int kb = u >> 7, ri = u & 1;
+          float sq[2], cq[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = kb * 4 + 2 * ri + h;
+            float sn = 0.f, cs = 0.f;
+            if (a_ok[i]) {
+              dev::sincos_cycles_mufu(dev::frac_of_product2(a_s[i], a_sl[i], ring_atom[tst][j].x) + a_s[i] * atl[j].x,
+                                      &sn, &cs);
+              const float w8 = atw[j];
+              sn *= w8;
+              cs *= w8;
+            }
+            sq[h] = sn;
+            cq[h] = cs;
+          }
+          float v[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int h = q & 1;
+            const float ps = __shfl_xor_sync(0xffffffffu, sq[h], 1), pc = __shfl_xor_sync(0xffffffffu, cq[h], 1);
+            const bool own = (q >> 1) == ri;
+            const float sn = own ? sq[h] : ps, cs = own ? cq[h] : pc;
+            v[2 * q] = ri ? sn : cs;
+            v[2 * q + 1] = ri ? cs : -sn;
+          }
+          uint4 hi, lo;
+          split2(v[0], v[1], hi.x, lo.x);
+          split2(v[2], v[3], hi.y, lo.y);
+          split2(v[4], v[5], hi.z, lo.z);
+          split2(v[6], v[7], hi.w, lo.w);
+          uint4* blk = reinterpret_cast<uint4*>(ringA + (bst * 2 + tp) * kPairTileBytes);
+          blk[u] = hi;
+          blk[512 + u] = lo;
+        }
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -504,14 +585,21 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
 
 cudaError_t sep_pair_prepare_kernel() {
   static_assert(kPairSmem + 8192 <= 227 * 1024, "dynamic + static shared memory of k_sep_pair");
-  return cudaFuncSetAttribute(k_sep_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_sep_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
+  return e != cudaSuccess
+             ? e
+             : cudaFuncSetAttribute(k_sep_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
 }
 
 // Grid: x = 2 CTAs x M quads x N tiles (cluster pairs along x), y = chunks.
 cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, cudaStream_t st) {
   const int64_t n_mq = ((a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2) + 1) / 2;
   dim3 grid((unsigned)(2 * n_mq * n_nt), (unsigned)n_chunks);
-  k_sep_pair<<<grid, kSepThreads, kPairSmem, st>>>(a);
+  if (a.form_a)
+    k_sep_pair<true><<<grid, kSepThreads, kPairSmem, st>>>(a);
+  else
+    k_sep_pair<false><<<grid, kSepThreads, kPairSmem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -660,7 +660,9 @@ int sep_best_split(const scatter_plan_s* p, int64_t tiles) {
   const double steps = (double)std::max<int64_t>(p->n_slots / kSepStep, 1);
   double best = 1e300;
   int best_k = 1;
-  for (int k = 1; k <= 64; ++k) {
+  // up to two chunks per SM: a grid of one N tile and one M quad (a few
+  // columns, a long atom list) needs ~n_sm / 2 chunks to give every SM a CTA
+  for (int k = 1; k <= 2 * p->n_sm; ++k) {
     if (k > 1 && steps / k < 64) break;
     // one step ~1 us of MMA; an extra chunk costs one partial of the
     // map (8 B per point written once, read once by the reduction)
@@ -747,7 +749,15 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   p->sep_nt = n_nt;
   p->sep_steps = n_steps;
   cudaError_t e;
-  const size_t a_bytes = (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
+  // With one N tile every A tile is read by one cluster only: the CTA pair
+  // then forms its A tiles itself from the atom records (the same arithmetic
+  // as k_sep_tab_a), and the table, written and read once, is not kept.
+  // With several N tiles that formation would repeat per tile, so the table
+  // stays; an odd pair count runs its last pair on the one-CTA kernel, which
+  // reads the table.
+  p->sep_form_a = sep_pair_enabled() && n_mp % 2 == 0 && n_nt == 1;
+  const size_t a_bytes =
+      p->sep_form_a ? 0 : (size_t)(2 * n_mp) * (size_t)std::max<int64_t>(n_steps, 1) * kSepABytes;
   // atom chunks: every species segment split into step-aligned pieces, about
   // `split` pieces in all, so that each chunk carries a single form factor
   std::vector<Segment> chunks;
@@ -767,10 +777,12 @@ scatter_status prepare_separable(scatter_plan_s* p, int split_override) {
   const size_t part_bytes =
       (size_t)p->sep_n_chunks * (size_t)sep_part_floats(n_mt, p->sep_n[1] * p->sep_n[2]) * sizeof(float);
   const size_t chunk_bytes = chunks.size() * sizeof(Segment);
-  if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
-  // tiles past the last row are never written by the table kernel: zero
-  // them once (the CTA-pair kernel streams the second tile of a pair always)
-  if ((e = cudaMemset(p->d.sep_A, 0, a_bytes)) != cudaSuccess) return cuda_status(e, "memset separable A");
+  if (a_bytes) {
+    if ((e = cudaMalloc(&p->d.sep_A, a_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc separable A");
+    // tiles past the last row are never written by the table kernel: zero
+    // them once (the CTA-pair kernel streams the second tile of a pair always)
+    if ((e = cudaMemset(p->d.sep_A, 0, a_bytes)) != cudaSuccess) return cuda_status(e, "memset separable A");
+  }
   if ((e = cudaMalloc(&p->d.sep_partial, part_bytes)) != cudaSuccess)
     return cuda_status(e, "cudaMalloc separable partials");
   if ((e = cudaMalloc(&p->d.sep_chunks, chunk_bytes)) != cudaSuccess) return cuda_status(e, "cudaMalloc chunks");
@@ -812,7 +824,7 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   t.n_mt = p->sep_mt;
   t.A = static_cast<uint4*>(p->d.sep_A);
   const int n_chunks = p->sep_n_chunks;
-  if (p->n_slots > 0) {
+  if (p->n_slots > 0 && !p->sep_form_a) {
     const int64_t na = p->sep_mt * p->sep_steps * 4 * kSepM;  // real tiles; a padding tile is never read
     k_sep_tab_a<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(t);
     p->last_launches += 1;
@@ -839,6 +851,9 @@ scatter_status launch_separable(scatter_plan_t p, float2* amp_out, float* int_ou
   a.partial = p->d.sep_partial;
   a.status = p->d.status;
   a.axis_att = p->d.sep_att;
+  a.form_a = p->sep_form_a ? 1 : 0;
+  a.rec_lo = p->d.atom_lo;
+  a.rec_w = p->d.atom_w;
   dim3 grid((unsigned)(((p->sep_mt + 1) / 2) * p->sep_nt), (unsigned)n_chunks);
   timing_begin(p, st);
   const cudaError_t le = sep_launch_core(a, grid, st, p->side_stream, p->side_fork, p->side_join);

@@ -64,6 +64,32 @@ def test_sphere_grids(shape, split):
     assert err < max(model, 1e-5) * 10
 
 
+@pytest.mark.parametrize("n0", [200, 130])
+def test_in_kernel_a_tiles_equal_the_table_route(n0):
+    """A grid of one N tile (every A tile read by one cluster) forms its A
+    tiles inside the CTA-pair kernel; a wider grid keeps the A table.  The
+    two forms compute the same A values in the same order, so the points the
+    two grids share agree bit for bit (same atom chunks).  n0 = 130 has a
+    zero padding tile in its second M-tile pair."""
+    c = W.fcc_sphere(radius_cells=6.2, seed=27)
+    occ = np.random.default_rng(28).uniform(0.5, 1.0, len(c.xyz)).astype(np.float32)
+    ax0 = W.linspace_axis(0.0, n0, step=0.004)
+    ax2 = W.linspace_axis(4.0, 9, step=0.004)
+    ax1_wide = W.linspace_axis(0.0, 64, step=0.004)
+    ax1_narrow = ax1_wide[:4]
+    narrow = api.Plan(c.coef, A_LAT, len(c.xyz), axes=[ax0, ax1_narrow, ax2], atom_species=c.species,
+                      path="separable", split_k=3)
+    wide = api.Plan(c.coef, A_LAT, len(c.xyz), axes=[ax0, ax1_wide, ax2], atom_species=c.species,
+                    path="separable", split_k=3)
+    An = run(narrow, c.xyz, occ).reshape(n0, 4, 9)
+    Aw = run(wide, c.xyz, occ).reshape(n0, 64, 9)
+    assert np.array_equal(An.view(np.float64), Aw[:, :4, :].copy().view(np.float64))
+    S = W.grid_points([ax0, ax1_narrow, ax2])
+    idx = np.sort(np.random.default_rng(29).choice(len(S), 512, replace=False))
+    ref = oracle.amplitude(c.xyz, S[idx], c.coef, A_LAT, species=c.species, occ=occ)
+    assert rel_l2(An.reshape(-1)[idx], ref) < TOL_TC
+
+
 def test_off_centre_and_generic_agree():
     c = W.fcc_sphere(radius_cells=3.5, seed=19)
     xyz = c.xyz + np.array([31.2, -17.9, 8.4])
