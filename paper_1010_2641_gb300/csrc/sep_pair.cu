@@ -52,6 +52,8 @@ constexpr uint32_t kPairTileBytes = kSepABytes;        // one CTA's A tile per s
 constexpr int kPairAStages = 4;
 constexpr int kPairBStages = kPairAStages;  // a step's A and B stages share one "ready" barrier
 constexpr int kPairTStages = 8;
+constexpr int kPairAWarps = 8;  // FORM_A: warps that form the A tiles (beside the B warps)
+constexpr int kPairThreadsA = kSepThreads + 32 * kPairAWarps;
 constexpr size_t kPairSmem = kPairAStages * 2 * kPairTileBytes + kPairBStages * kPairBBytes + 1024;
 // kind::f16, D f32, K-major A and B, N = 256 (>> 3 at bit 17), M = 256 (>> 4 at bit 24)
 constexpr uint32_t kPairIdesc = (1u << 4) | ((uint32_t)(kSepN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
@@ -131,12 +133,13 @@ __device__ __forceinline__ void commit_pair(uint64_t* bar) {
 //   bar_tempty[t] atom records read by this CTA's formation     (8 warps)
 //   bar_tread     this CTA's accumulators read out              (8 warps)
 //   bar_pfree     rank 0: rank 1's accumulators read out        (relay)
-// FORM_A: the formation warps also form this CTA's A tiles from the step's
-// atom records (with their x' errors and occupancies) instead of the copy
-// warp streaming them from the table (a grid of one N tile, where the table
-// would be written and read once).
+// FORM_A: eight more warps (10..17, kPairThreadsA threads per CTA) form this
+// CTA's A tiles from the step's atom records (with their x' errors and
+// occupancies) instead of the copy warp streaming them from the table (a
+// grid of one N tile, where the table would be written and read once); they
+// wait and signal like the B warps, and take no part in the read-outs.
 template <bool FORM_A>
-__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepArgs a) {
+__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(FORM_A ? 112 : 168) k_sep_pair(const SepArgs a) {
   extern __shared__ __align__(1024) unsigned char pair_smem_raw[];
   __shared__ __align__(8) uint64_t bar_ready[kPairAStages];
   __shared__ __align__(8) uint64_t bar_done[kPairAStages];
@@ -156,6 +159,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   unsigned char* ringB = smem + kPairAStages * 2 * kPairTileBytes;  // [stage][hi 8 KB | lo 8 KB]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool mma_warp = warp == kSepFormWarps, copy_warp = warp == kSepFormWarps + 1;
+  const bool a_warp = FORM_A && warp >= kSepFormWarps + 2;
   const uint32_t rank = cluster_rank();
   const int64_t n_mp = a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2;  // M-tile pairs of this launch
   const int64_t n_mq = (n_mp + 1) / 2;       // M quads (one per cluster)
@@ -183,12 +187,12 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
   }
   if (tid == 0) {
     for (int s = 0; s < kPairAStages; ++s) {
-      dev::mbar_init(&bar_ready[s], (FORM_A ? 0 : 1) + kSepFormWarps + (rank == 0 ? 1 : 0));
+      dev::mbar_init(&bar_ready[s], (FORM_A ? kPairAWarps : 1) + kSepFormWarps + (rank == 0 ? 1 : 0));
       dev::mbar_init(&bar_done[s], 1);
     }
     for (int s = 0; s < kPairTStages; ++s) {
       dev::mbar_init(&bar_atom[s], 1);
-      dev::mbar_init(&bar_tempty[s], kSepFormWarps);
+      dev::mbar_init(&bar_tempty[s], kSepFormWarps + (FORM_A ? kPairAWarps : 0));
     }
     dev::mbar_init(&bar_tread, kSepFormWarps);
     dev::mbar_init(&bar_pfree, 1);
@@ -323,6 +327,89 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         }
       }
     }
+  } else if (a_warp) {
+    // ---- FORM_A: the A warps -------------------------------------------------
+    // unit i * 256 + atid of the CTA's 2 x 512 16-byte rows of a step's A
+    // tiles (the table kernel's units: 4 atoms of one row m in one K block);
+    // m = 2 a + {Re, Im}, and the two lanes of a row pair share
+    // X = w e^{2 pi i s_a x'} of their 4 atoms
+    const int atid = tid - 32 * (kSepFormWarps + 2);
+    constexpr int kAUnits = 4;
+    float a_s[kAUnits], a_sl[kAUnits];
+    bool a_ok[kAUnits];
+#pragma unroll
+    for (int i = 0; i < kAUnits; ++i) {
+      const int unit = i * 256 + atid, tp = unit >> 9, u = unit & 511;
+      const int64_t m = (int64_t)(2 * (mp0 + tp) + (int)rank) * kSepM + ((u >> 3) & 15) * 8 + (u & 7);
+      const int64_t ah = m >> 1;
+      a_ok[i] = tp < ntp && ah < a.n0;
+      a_s[i] = a_ok[i] ? a.axis_s[ah] : 0.f;
+      a_sl[i] = a_ok[i] ? a.axis_lo[ah] : 0.f;
+    }
+    int64_t g = 0;
+    for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
+      const int bst = (int)(g % kPairBStages), tst = (int)(g % kPairTStages);
+      bool w = !s_abort;
+      if (w && g >= kPairBStages)
+        w = dev::mbar_wait_bounded(&bar_done[(g - kPairBStages) % kPairAStages],
+                                   (uint32_t)(((g - kPairBStages) / kPairAStages) & 1));
+      if (w) w = dev::mbar_wait_bounded(&bar_atom[tst], (uint32_t)((g / kPairTStages) & 1));
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        break;
+      }
+      // the step's A tiles of this CTA (rows of M tile 2 (mp0 + tp) + rank of
+      // every tile pair with rows), as the table kernel writes them: the
+      // phase s_a x' with its products' rounding errors restored, MUFU
+      // sin/cos, the occupancy, rows Re (Xr, -Xi) and Im (Xi, Xr), f16 hi, lo
+      const float4* atl = ring_lo[tst];
+      const float* atw = ring_w[tst];
+#pragma unroll
+      for (int i = 0; i < kAUnits; ++i) {
+        const int unit = i * 256 + atid, tp = unit >> 9, u = unit & 511;
+        if (tp >= ntp) continue;  // the same for the whole warp
+        const int kb = u >> 7, ri = u & 1;
+        float sq[2], cq[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = kb * 4 + 2 * ri + h;
+          float sn = 0.f, cs = 0.f;
+          if (a_ok[i]) {
+            dev::sincos_cycles_mufu(dev::frac_of_product2(a_s[i], a_sl[i], ring_atom[tst][j].x) + a_s[i] * atl[j].x,
+                                    &sn, &cs);
+            const float w8 = atw[j];
+            sn *= w8;
+            cs *= w8;
+          }
+          sq[h] = sn;
+          cq[h] = cs;
+        }
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int h = q & 1;
+          const float ps = __shfl_xor_sync(0xffffffffu, sq[h], 1), pc = __shfl_xor_sync(0xffffffffu, cq[h], 1);
+          const bool own = (q >> 1) == ri;
+          const float sn = own ? sq[h] : ps, cs = own ? cq[h] : pc;
+          v[2 * q] = ri ? sn : cs;
+          v[2 * q + 1] = ri ? cs : -sn;
+        }
+        uint4 hi, lo;
+        split2(v[0], v[1], hi.x, lo.x);
+        split2(v[2], v[3], hi.y, lo.y);
+        split2(v[4], v[5], hi.z, lo.z);
+        split2(v[6], v[7], hi.w, lo.w);
+        uint4* blk = reinterpret_cast<uint4*>(ringA + (bst * 2 + tp) * kPairTileBytes);
+        blk[u] = hi;
+        blk[512 + u] = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bar_ready[bst]);
+        mbar_arrive(&bar_tempty[tst]);
+      }
+    }
   } else {
     // ---- formation warps ---------------------------------------------------
     // column col of this CTA's half: forward the point (b, c) with offsets
@@ -362,22 +449,6 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         reduce = bound > kSepPhaseLim;
         exact = bound > dev::kPhaseExactLim;
       }
-    }
-    // FORM_A: this thread's four 16-byte rows of the step's A tiles (the
-    // table kernel's units: 4 atoms of one row m in one K block), unit
-    // i * 256 + tid of the CTA's 2 x 512; m = 2 a + {Re, Im}, and the two
-    // lanes of a row pair share X = w e^{2 pi i s_a x'} of their 4 atoms
-    constexpr int kAUnits = FORM_A ? 4 : 1;
-    float a_s[kAUnits], a_sl[kAUnits];
-    bool a_ok[kAUnits];
-#pragma unroll
-    for (int i = 0; i < kAUnits; ++i) {
-      const int unit = i * 256 + tid, tp = unit >> 9, u = unit & 511;
-      const int64_t m = (int64_t)(2 * (mp0 + tp) + (int)rank) * kSepM + ((u >> 3) & 15) * 8 + (u & 7);
-      const int64_t ah = m >> 1;
-      a_ok[i] = FORM_A && tp < ntp && ah < a.n0;
-      a_s[i] = a_ok[i] ? a.axis_s[ah] : 0.f;
-      a_sl[i] = a_ok[i] ? a.axis_lo[ah] : 0.f;
     }
     float* part = a.partial + (int64_t)chunk * a.chunk_floats;
     bool first_flush = true;
@@ -445,53 +516,6 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(168) k_sep_pair(const SepA
         form_all(std::true_type{});
       else
         form_all(std::false_type{});
-      if constexpr (FORM_A) {
-        // the step's A tiles of this CTA (rows of M tile 2 (mp0 + tp) + rank
-        // of every tile pair with rows), as the table kernel writes them: the phase
-        // s_a x' with its products' rounding errors restored, MUFU sin/cos,
-        // the occupancy, rows Re (Xr, -Xi) and Im (Xi, Xr), f16 hi and lo
-        const float4* atl = ring_lo[tst];
-        const float* atw = ring_w[tst];
-#pragma unroll
-        for (int i = 0; i < kAUnits; ++i) {
-          const int unit = i * 256 + tid, tp = unit >> 9, u = unit & 511;
-          if (tp >= ntp) continue;  // the same for the whole warp
-          const int kb = u >> 7, ri = u & 1;
-          float sq[2], cq[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int j = kb * 4 + 2 * ri + h;
-            float sn = 0.f, cs = 0.f;
-            if (a_ok[i]) {
-              dev::sincos_cycles_mufu(dev::frac_of_product2(a_s[i], a_sl[i], ring_atom[tst][j].x) + a_s[i] * atl[j].x,
-                                      &sn, &cs);
-              const float w8 = atw[j];
-              sn *= w8;
-              cs *= w8;
-            }
-            sq[h] = sn;
-            cq[h] = cs;
-          }
-          float v[8];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int h = q & 1;
-            const float ps = __shfl_xor_sync(0xffffffffu, sq[h], 1), pc = __shfl_xor_sync(0xffffffffu, cq[h], 1);
-            const bool own = (q >> 1) == ri;
-            const float sn = own ? sq[h] : ps, cs = own ? cq[h] : pc;
-            v[2 * q] = ri ? sn : cs;
-            v[2 * q + 1] = ri ? cs : -sn;
-          }
-          uint4 hi, lo;
-          split2(v[0], v[1], hi.x, lo.x);
-          split2(v[2], v[3], hi.y, lo.y);
-          split2(v[4], v[5], hi.z, lo.z);
-          split2(v[6], v[7], hi.w, lo.w);
-          uint4* blk = reinterpret_cast<uint4*>(ringA + (bst * 2 + tp) * kPairTileBytes);
-          blk[u] = hi;
-          blk[512 + u] = lo;
-        }
-      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
@@ -597,7 +621,7 @@ cudaError_t sep_pair_launch_core(const SepArgs& a, int64_t n_nt, int n_chunks, c
   const int64_t n_mq = ((a.mp_count > 0 ? a.mp_count : (a.n_mt + 1) / 2) + 1) / 2;
   dim3 grid((unsigned)(2 * n_mq * n_nt), (unsigned)n_chunks);
   if (a.form_a)
-    k_sep_pair<true><<<grid, kSepThreads, kPairSmem, st>>>(a);
+    k_sep_pair<true><<<grid, kPairThreadsA, kPairSmem, st>>>(a);
   else
     k_sep_pair<false><<<grid, kSepThreads, kPairSmem, st>>>(a);
   return cudaGetLastError();
