@@ -8,8 +8,9 @@ every call reuses what the previous call left there.  These tests check its
 result (f == 1) against the oracle element by element on calls in a row of
 different sizes, on a crystal far from the origin, on a long chain that
 takes the exact-product phases, at the largest sizes it accepts (sampled),
-and that a non-finite input poisons the whole output while the next call is
-clean again.  The plan-based call is a second reference.  This file is
+that a non-finite input poisons the whole output while the next call is
+clean again, and a call captured into a CUDA graph and replayed on new
+inputs in the same buffers.  The plan-based call is a second reference.  This file is
 collected last so that a failure here, in a run that stops at the first
 failure, comes after every other test.
 """
@@ -123,6 +124,41 @@ def test_noalloc_at_the_size_limits_sampled():
     assert np.all(np.isfinite(got))
     idx = rng.choice(MAX_POINTS, 96, replace=False)
     assert rel_l2(got[idx], oracle.amplitude(xyz, S[idx], UNIT, W.LATTICE_A)) < TOL
+
+
+def test_noalloc_captured_in_a_graph_and_replayed_on_new_inputs():
+    """What the entry point is for: after one call outside capture (which
+    looks its scratch up), a call is captured into a CUDA graph, new inputs
+    are written into the same buffers and the graph replays them."""
+    dev = torch.device("cuda:0")
+    xyz, occ, S = _case(61, 3000, 2500)
+    x = torch.tensor(xyz, dtype=torch.float64, device=dev)
+    w = torch.tensor(occ, dtype=torch.float32, device=dev)
+    s = torch.tensor(S, dtype=torch.float64, device=dev)
+    out = torch.full((len(S),), float("nan"), dtype=torch.complex64, device=dev)
+    h = (ctypes.c_double * 3)(0.0, 0.0, 4.0)
+
+    def call(stream):
+        B.check(B.lib().scatter_amplitude_noalloc(len(xyz), x.data_ptr(), w.data_ptr(), len(S), s.data_ptr(), h,
+                                                  out.data_ptr(), stream.cuda_stream), "scatter_amplitude_noalloc")
+
+    call(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ref1 = oracle.amplitude(xyz, S, UNIT, W.LATTICE_A, occ=occ)
+    assert rel_l2(out.cpu().numpy().astype(np.complex128), ref1) < TOL
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        call(side)
+    xyz2, occ2, S2 = _case(62, 3000, 2500, offset=3.0)
+    x.copy_(torch.tensor(xyz2, dtype=torch.float64))
+    w.copy_(torch.tensor(occ2, dtype=torch.float32))
+    s.copy_(torch.tensor(S2, dtype=torch.float64))
+    out.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    ref2 = oracle.amplitude(xyz2, S2, UNIT, W.LATTICE_A, occ=occ2)
+    assert rel_l2(out.cpu().numpy().astype(np.complex128), ref2) < TOL
 
 
 def test_noalloc_rejects_oversize():
