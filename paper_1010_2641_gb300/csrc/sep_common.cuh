@@ -91,6 +91,47 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t&
   asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(y - hf.y), "f"(x - hf.x));
 }
 
+// One 16-byte row of the A operand's core matrix, hi and lo: row m = 2 a +
+// ri (Re or Im of axis value a, offset s_a = sa + sal) over one K block of 4
+// atoms.  Lanes l and l ^ 1 hold rows 2 a and 2 a + 1 of the same a and
+// share X_j = w_j e^{2 i pi s_a x'_j}: lane ri evaluates atoms 2 ri, 2 ri + 1
+// of the block (x'_j with its rounding error xl_j, weight w_j) and takes the
+// other two from its neighbour.  The phase is reduced exactly mod 1 (the
+// products' rounding errors restored) before the MUFU sin/cos: |error| <
+// 4e-7, below the hi + lo split's resolution.  Row 2 a holds (Xr, -Xi), row
+// 2 a + 1 (Xi, Xr).  All 32 lanes of the warp must call it together (ok
+// false gives a zero row).  The table kernel and the CTA pair's A warps
+// both form A through it, so the two routes agree bit for bit.
+__device__ __forceinline__ void sep_a_row(float sa, float sal, bool ok, int ri, const float (&x)[2],
+                                          const float (&xl)[2], const float (&w)[2], uint4& hi, uint4& lo) {
+  float sq[2], cq[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float sn = 0.f, cs = 0.f;
+    if (ok) {
+      dev::sincos_cycles_mufu(dev::frac_of_product2(sa, sal, x[h]) + sa * xl[h], &sn, &cs);
+      sn *= w[h];
+      cs *= w[h];
+    }
+    sq[h] = sn;
+    cq[h] = cs;
+  }
+  float v[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int h = q & 1;
+    const float ps = __shfl_xor_sync(0xffffffffu, sq[h], 1), pc = __shfl_xor_sync(0xffffffffu, cq[h], 1);
+    const bool own = (q >> 1) == ri;
+    const float sn = own ? sq[h] : ps, cs = own ? cq[h] : pc;
+    v[2 * q] = ri ? sn : cs;
+    v[2 * q + 1] = ri ? cs : -sn;
+  }
+  split2(v[0], v[1], hi.x, lo.x);
+  split2(v[2], v[3], hi.y, lo.y);
+  split2(v[4], v[5], hi.z, lo.z);
+  split2(v[6], v[7], hi.w, lo.w);
+}
+
 struct SepArgs {
   const uint4* A;         // A blocks [species][M-tile pair][step][2 tiles][hi|lo] of 16 KB per tile
   int64_t a_sp_stride;    // uint4 per species table of A (0: one table, the forward)

@@ -369,36 +369,16 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(FORM_A ? 112 : 168) k_sep_
         const int unit = i * 256 + atid, tp = unit >> 9, u = unit & 511;
         if (tp >= ntp) continue;  // the same for the whole warp
         const int kb = u >> 7, ri = u & 1;
-        float sq[2], cq[2];
+        float x[2], xl[2], w[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int j = kb * 4 + 2 * ri + h;
-          float sn = 0.f, cs = 0.f;
-          if (a_ok[i]) {
-            dev::sincos_cycles_mufu(dev::frac_of_product2(a_s[i], a_sl[i], ring_atom[tst][j].x) + a_s[i] * atl[j].x,
-                                    &sn, &cs);
-            const float w8 = atw[j];
-            sn *= w8;
-            cs *= w8;
-          }
-          sq[h] = sn;
-          cq[h] = cs;
-        }
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int h = q & 1;
-          const float ps = __shfl_xor_sync(0xffffffffu, sq[h], 1), pc = __shfl_xor_sync(0xffffffffu, cq[h], 1);
-          const bool own = (q >> 1) == ri;
-          const float sn = own ? sq[h] : ps, cs = own ? cq[h] : pc;
-          v[2 * q] = ri ? sn : cs;
-          v[2 * q + 1] = ri ? cs : -sn;
+          x[h] = ring_atom[tst][j].x;
+          xl[h] = atl[j].x;
+          w[h] = atw[j];
         }
         uint4 hi, lo;
-        split2(v[0], v[1], hi.x, lo.x);
-        split2(v[2], v[3], hi.y, lo.y);
-        split2(v[4], v[5], hi.z, lo.z);
-        split2(v[6], v[7], hi.w, lo.w);
+        sep_a_row(a_s[i], a_sl[i], a_ok[i], ri, x, xl, w, hi, lo);
         uint4* blk = reinterpret_cast<uint4*>(ringA + (bst * 2 + tp) * kPairTileBytes);
         blk[u] = hi;
         blk[512 + u] = lo;

@@ -80,43 +80,20 @@ __global__ void k_sep_tab_a(const SepTabArgs t) {
   const int64_t m = mt * kSepM + mg * 8 + r;
   const int64_t a = m >> 1;
   const int ri = (int)(m & 1);
-  // lanes 2a' and 2a'+1 (rows Re and Im of the same h) share X(h, atom):
-  // each evaluates two of the block's four atoms and takes the other two
-  // from its neighbour
-  float sq[2], cq[2];
-  const float sa = a < t.n0 ? t.axis_s[a] : 0.f, sal = a < t.n0 ? t.axis_lo[a] : 0.f;
+  const bool ok = a < t.n0;
+  const float sa = ok ? t.axis_s[a] : 0.f, sal = ok ? t.axis_lo[a] : 0.f;
+  float x[2] = {0.f, 0.f}, xl[2] = {0.f, 0.f}, w[2] = {0.f, 0.f};
+  if (ok) {
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int64_t slot = ks * kSepStep + kb * 4 + 2 * ri + u;
-    float sn = 0.f, cs = 0.f;
-    if (a < t.n0) {
-      // the phase reduced exactly mod 1 (products with their rounding errors
-      // restored), then MUFU sin/cos as for the formed rows: |error| < 4e-7,
-      // below the f16 hi + lo split's resolution
-      dev::sincos_cycles_mufu(dev::frac_of_product2(sa, sal, t.atom4[slot].x) + sa * t.atom_lo[slot].x, &sn, &cs);
-      const float w = t.atom_w[slot];
-      sn *= w;
-      cs *= w;
+    for (int u = 0; u < 2; ++u) {
+      const int64_t slot = ks * kSepStep + kb * 4 + 2 * ri + u;
+      x[u] = t.atom4[slot].x;
+      xl[u] = t.atom_lo[slot].x;
+      w[u] = t.atom_w[slot];
     }
-    sq[u] = sn;
-    cq[u] = cs;
-  }
-  float v[8];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int u = q & 1;
-    const float ps = __shfl_xor_sync(0xffffffffu, sq[u], 1), pc = __shfl_xor_sync(0xffffffffu, cq[u], 1);
-    const bool own = (q >> 1) == ri;
-    const float sn = own ? sq[u] : ps, cs = own ? cq[u] : pc;
-    // row 2a: (Xr, -Xi); row 2a+1: (Xi, Xr)
-    v[2 * q] = ri ? sn : cs;
-    v[2 * q + 1] = ri ? cs : -sn;
   }
   uint4 hi, lo;
-  split2(v[0], v[1], hi.x, lo.x);
-  split2(v[2], v[3], hi.y, lo.y);
-  split2(v[4], v[5], hi.z, lo.z);
-  split2(v[6], v[7], hi.w, lo.w);
+  sep_a_row(sa, sal, ok, ri, x, xl, w, hi, lo);
   uint4* blk = t.A + (((mt >> 1) * t.n_steps + ks) * kSepPair + (mt & 1)) * (kSepABytes / 16);
   const int64_t off = (int64_t)(kb * 16 + mg) * 8 + r;
   blk[off] = hi;
