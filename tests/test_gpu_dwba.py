@@ -55,6 +55,22 @@ def test_small_island_vs_oracle(path, tol, n_af):
     assert rel_l2(A, ref) < tol
 
 
+@pytest.mark.parametrize("n_h", [300, 130])
+def test_separable_virtual_grid_of_several_m_tile_pairs(n_h):
+    """The four beams' virtual grid with 300 h values (600 rows: 3 M-tile
+    pairs, two on the CTA pair and the last on the one-CTA kernel beside it)
+    and 130 (2 pairs, the second with a padding tile) against the oracle on
+    sampled points."""
+    c = small_island()
+    axes = [np.linspace(3.7, 4.3, n_h), np.linspace(-0.05, 0.05, 3), np.deg2rad(np.linspace(0.05, 0.6, 5))]
+    A, _ = gpu_map(c, axes, path="separable")
+    S = gid_points(axes)
+    idx = np.sort(np.random.default_rng(5).choice(len(S), 600, replace=False))
+    ref = oracle.dwba(c.xyz, S[idx], c.coef, A_LAT, LAM, W.GID_ALPHA_I, W.GID_DELTA, W.GID_BETA,
+                      species=c.species)
+    assert rel_l2(A[idx], ref) < 1e-3
+
+
 @pytest.mark.parametrize("path,tol", [("generic", 1e-4), ("separable", 1e-3)])
 def test_occupancy_and_split(path, tol):
     c = small_island()

@@ -38,8 +38,10 @@ def _device_map(plan, xyz, occ=None):
 
 
 # n0 = 40 -> 80 map rows -> three 32-row blocks: three ragged copy ranges;
-# n0 = 3 -> one block: one range; n0 = 128 -> eight blocks in four ranges
-@pytest.mark.parametrize("shape", [(40, 12, 20), (3, 33, 17), (128, 16, 8)])
+# n0 = 3 -> one block: one range; n0 = 128 -> eight blocks in four ranges;
+# n0 = 384 -> three M-tile pairs: the contraction's last pair runs on the
+# plan's side stream beside the CTA-pair kernel, then the ranges are copied
+@pytest.mark.parametrize("shape", [(40, 12, 20), (3, 33, 17), (128, 16, 8), (384, 4, 9)])
 def test_separable_grid_ranges_copied_while_reducing(shape):
     c = W.fcc_sphere(radius_cells=4.5, seed=71)
     occ = np.random.default_rng(72).uniform(0.5, 1.0, len(c.xyz)).astype(np.float32)
