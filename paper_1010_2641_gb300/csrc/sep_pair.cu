@@ -214,7 +214,8 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(FORM_A ? 112 : 168) k_sep_
     if (lane == 0) {
       // this CTA's A tile of each pair with rows (half `rank` of the pair's
       // (pair, step) block) and the step's K records, in step order
-      const uint4* Abase = a.A + a_species * a.a_sp_stride + rank * (kPairTileBytes / 16);
+      // (FORM_A: no A table, a.A is null and never read)
+      const uint4* Abase = FORM_A ? nullptr : a.A + a_species * a.a_sp_stride + rank * (kPairTileBytes / 16);
       const int64_t pair_stride = a.n_steps * (kSepPair * kSepABytes / 16);
       int64_t g = 0;
       for (int64_t ks = ks_begin; ks < ks_end; ++ks, ++g) {
