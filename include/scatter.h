@@ -276,9 +276,9 @@ scatter_status scatter_amplitude(scatter_plan_t plan, const double* xyz,
  *
  * The plan copies the inputs into device buffers of its own (allocated on
  * the first host call and kept until scatter_plan_destroy: 28 n_atoms + 8 n_s
- * bytes, plus a second stream and five events), runs the plan's forward on
+ * bytes, plus a second stream and 17 events), runs the plan's forward on
  * them and copies the map back.  On a SEPARABLE plan of a GRID the final
- * reduction runs in four ranges of map rows and each range's copy to the
+ * reduction runs in up to 16 ranges of map rows and each range's copy to the
  * host starts on the plan's second stream as soon as that range is reduced,
  * overlapping the rest of the reduction; `stream` waits for the last copy.
  * Pinned host memory gives asynchronous copies; pageable memory is accepted

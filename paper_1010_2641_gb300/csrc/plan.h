@@ -82,8 +82,9 @@ struct Tiling {
 };
 
 // row ranges of a separable map reduced and copied out one after another by
-// scatter_amplitude_host
-constexpr int kHostPieces = 4;
+// scatter_amplitude_host (at most one per 32-row block of partials): the
+// more ranges, the less of the map's copy is left after the last reduction
+constexpr int kHostPieces = 16;
 
 struct DeviceBuffers {
   int32_t* slot_src = nullptr;      // [n_slots]

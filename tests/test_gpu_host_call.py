@@ -38,7 +38,7 @@ def _device_map(plan, xyz, occ=None):
 
 
 # n0 = 40 -> 80 map rows -> three 32-row blocks: three ragged copy ranges;
-# n0 = 3 -> one block: one range; n0 = 128 -> eight blocks in four ranges;
+# n0 = 3 -> one block: one range; n0 = 128 -> eight blocks in eight ranges;
 # n0 = 384 -> three M-tile pairs: the contraction's last pair runs on the
 # plan's side stream beside the CTA-pair kernel, then the ranges are copied
 @pytest.mark.parametrize("shape", [(40, 12, 20), (3, 33, 17), (128, 16, 8), (384, 4, 9)])
@@ -80,7 +80,7 @@ def test_generic_list_with_pageable_buffers():
     assert rel_l2(out.numpy().astype(np.complex128), ref2) < 1e-4
 
 
-def test_bench_map_four_ranges_equal_the_device_call():
+def test_bench_map_sixteen_ranges_equal_the_device_call():
     c = W.fcc_sphere()
     axes = [W.linspace_axis(0.0, 256, step=0.002), W.linspace_axis(0.0, 256, step=0.002),
             W.linspace_axis(4.0, 64, step=0.002)]
