@@ -105,10 +105,17 @@ def test_off_centre_and_generic_agree():
     assert ps.info()["shift"] == [31.0, -18.0, 8.0]
 
 
-def test_no_atoms():
-    axes = [np.array([0.0, 0.1]), np.array([0.0]), np.array([4.0, 4.1, 4.2])]
+@pytest.mark.parametrize("n0", [2, 200, 300])
+def test_no_atoms(n0):
+    """An empty crystal gives a zero map on the one-CTA kernel (n0 = 2),
+    on the CTA pair forming its own A tiles (n0 = 200: two M-tile pairs, one
+    N tile) and on the CTA pair with the one-CTA kernel beside it (n0 = 300:
+    three pairs)."""
+    axes = [W.linspace_axis(0.0, n0, step=0.01), np.array([0.0]), np.array([4.0, 4.1, 4.2])]
     plan = api.Plan(W.unit_species()[None], A_LAT, 0, axes=axes, path="separable")
     A = plan.amplitude(torch.empty(0, 3, dtype=torch.float64, device="cuda:0"))
+    plan.check()
+    assert A.shape == (n0 * 3,)
     assert torch.all(A == 0)
 
 
